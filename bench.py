@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the weak-distance hot path on B300: G triangle-frequency pairs/s.
+
+Default workload ("sweep"): icosahedral meshes n = 8, 16, 32, 64 (1,280 to
+81,920 triangles) against the unit sphere for s = 1 and s = 2, on the ball rule
+R = 128 with 192 radial x 96 polar x 192 azimuthal nodes and Hermitian halving
+(1,769,472 evaluated nodes). One step = the 8 distance queries, i.e. every
+(triangle, node) pair of every query: stage the mesh, evaluate the exact
+triangle transforms, sum per node, subtract the sphere, weight and reduce.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "G triangle-freq pairs/s + distance queries/s (p50/p99) at 1e-6 rel err vs plain FP64"
+UNIT = "Gpair/s"
+
+# Algorithmic work of one (triangle, node) pair of the mixed path: the upper
+# end of the per-pair estimate (FP32 pipe operations and MUFU operations) for
+# the exact divided-difference evaluation with float32 transcendental
+# arithmetic. The pipe bound per SM per clock is max(N_FP32/128, N_MUFU/16).
+N_FP32_PER_PAIR = 60
+N_MUFU_PER_PAIR = 6
+L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["sweep", "large", "small"], default="sweep")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-check", action="store_true", help="skip the mixed-vs-fp64 accuracy check")
+    p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def workload(name):
+    """(description dict, list of (verts, tris, s) queries, rule descriptor)."""
+    if name == "sweep":
+        R = synth.SWEEP_RULE
+        meshes = [synth.icosphere(n) for n in synth.SWEEP_NS]
+        queries = [(v, t, s) for (v, t) in meshes for s in synth.SWEEP_SS]
+        cfg = {"workload": "icosahedral refinement sweep n=8,16,32,64 vs unit sphere, s in {1,2}",
+               "n": list(synth.SWEEP_NS), "s": list(synth.SWEEP_SS)}
+    elif name == "large":
+        R = synth.LARGE_RULE
+        v, t = synth.large_mesh()
+        queries = [(v, t, synth.LARGE_S)]
+        cfg = {"workload": "icosahedral n=128 (327,680 triangles), radial jitter 1e-4 seed 7, s=1",
+               "n": [synth.LARGE_N], "s": [synth.LARGE_S]}
+    else:
+        R = synth.SMALL_RULE
+        v, t = synth.icosphere(synth.SMALL_N)
+        queries = [(v, t, synth.SMALL_S)]
+        cfg = {"workload": "icosahedral n=4 (320 triangles) vs unit sphere, s=1",
+               "n": [synth.SMALL_N], "s": [synth.SMALL_S]}
+    cfg.update({"rule": "ball R=%g, %d radial x %d polar x %d azimuth%s" % (
+        R.R, R.n_r, R.n_polar, R.n_azim, ", hermitian" if R.hermitian else ""),
+        "nodes_evaluated": R.n_eval(), "nodes_total": R.n_r * R.n_polar * R.n_azim})
+    return cfg, queries, R
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.rows = []
+        self.proc = None
+        self.device = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "", 1).isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for name, val in zip(names, r[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        loaded = [x for x in sm if x > 0.5 * (max(mx) if mx else 0)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2032.0}, "fallback"
+
+
+def pair_roofline_peak(sm_count, mhz):
+    clk_per_pair = max(N_FP32_PER_PAIR / 128.0, N_MUFU_PER_PAIR / 16.0)
+    return sm_count * mhz * 1e6 / clk_per_pair
+
+
+def cpu_baseline(R, queries, seconds):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    xi, w = oracle.ball_rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+    v, t, s = queries[0]
+    threads = oracle.default_threads()
+    # calibrate on growing probes, then size the sample to about `seconds`
+    m = 64
+    while True:
+        idx = np.arange(0, len(xi), max(1, len(xi) // m))[:m]
+        t0 = time.perf_counter()
+        oracle.distance(xi[idx], w[idx], s, v, t, nthreads=threads)
+        dt = time.perf_counter() - t0
+        if dt > 0.3 or m >= len(xi):
+            break
+        m *= 4
+    rate = len(idx) * len(t) / max(dt, 1e-6)
+    n_nodes = int(min(len(xi), max(64, rate * seconds / len(t))))
+    stride = max(1, len(xi) // n_nodes)
+    idx = np.arange(0, len(xi), stride)[:n_nodes]
+    t0 = time.perf_counter()
+    oracle.distance(xi[idx], w[idx], s, v, t, nthreads=threads)
+    dt = time.perf_counter() - t0
+    pairs = len(idx) * len(t)
+    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "long-double oracle distance, first query's mesh (%d triangles) on every %d-th node "
+                      "of the rule (%d nodes, %.3g pairs, %.1f s)" % (len(t), stride, len(idx), pairs, dt)}
+
+
+def run_reference(args, cfg, queries, R):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(3.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(R, queries, min(per_step, 3.0))
+    vals = []
+    t_all = 0.0
+    cb = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(R, queries, per_step)
+        t_all += time.perf_counter() - t0
+        vals.append(cb["value"])
+    value = statistics.median(vals) if vals else 0.0
+    if cb is not None:
+        cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f80",
+            "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    cfg, queries, R = workload(args.workload)
+    cfg["precision"] = args.precision
+    cfg["l2"] = "flushed between timed steps (%d MB write)" % (L2_FLUSH_BYTES >> 20)
+    if args.impl == "reference":
+        run_reference(args, cfg, queries, R)
+        return
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2304_06340_b300 as wd
+    prec = wd.WD_MIXED if args.precision == "mixed" else wd.WD_FP64
+    ctx = wd.Context(local)
+    rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+    n_eval, n_total = wd.wd_rule_info(rule)
+    dq = [(torch.tensor(v, device=dev), torch.tensor(t, device=dev), s) for (v, t, s) in queries]
+    out = torch.zeros(len(dq), dtype=torch.float64, device=dev)
+    pairs_per_step = sum(t.shape[0] for (_, t, _) in dq) * n_eval
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = ctx.handle
+
+    def step():
+        for i, (v, t, s) in enumerate(dq):
+            wd.wd_distance_dev(h, rule, v, t, None, s, prec, out[i:i + 1], stream)
+
+    for _ in range(args.warmup):
+        step()
+    wd.wd_sync(h, stream)
+
+    # ---- timed region (device events per step; L2 flushed before each step)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launches()
+    evs = []
+    qevs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        marks = []
+        for i, (v, t, s) in enumerate(dq):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wd.wd_distance_dev(h, rule, v, t, None, s, prec, out[i:i + 1], stream)
+            e1.record(stream)
+            marks.append((e0, e1, t.shape[0]))
+        b.record(stream)
+        evs.append((a, b))
+        qevs.append(marks)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = ctx.launches() - launches0
+    clk = clocks.stop()
+    wd.wd_sync(h, stream)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = tt.item()
+    value = world * pairs_per_step * args.steps / total_s / 1e9
+    # per-query kernel time (stage + pair kernel; the stage kernel is O(T) and under 0.1%)
+    q_ms = [e0.elapsed_time(e1) for marks in qevs for (e0, e1, _) in marks]
+    q_pairs = [T * n_eval for marks in qevs for (_, _, T) in marks]
+    pair_rate = sum(q_pairs) / (sum(q_ms) / 1e3)
+    lat = sorted(q_ms)
+    d_values = out.cpu().tolist()
+
+    # ---- accuracy of the mixed path against the float64 path (two smallest meshes)
+    accuracy = None
+    if prec == wd.WD_MIXED and not args.no_check:
+        errs = []
+        for i, (v, t, s) in enumerate(dq):
+            if t.shape[0] > 6000:
+                continue
+            ref = torch.zeros(1, dtype=torch.float64, device=dev)
+            wd.wd_distance_dev(h, rule, v, t, None, s, wd.WD_FP64, ref, stream)
+            wd.wd_sync(h, stream)
+            errs.append(abs(d_values[i] - ref.item()) / ref.item())
+        accuracy = {"max_rel_err_vs_fp64": max(errs) if errs else None, "queries_checked": len(errs)}
+
+    # ---- end to end through the host-buffer C-ABI call (pinned host inputs)
+    pinned = []
+    for (v, t, s) in queries:
+        pv = torch.empty((len(v), 3), dtype=torch.float64).pin_memory()
+        pt = torch.empty((len(t), 3), dtype=torch.int32).pin_memory()
+        pv.copy_(torch.from_numpy(v))
+        pt.copy_(torch.from_numpy(t))
+        pinned.append((pv.numpy(), pt.numpy(), s))
+    for (v, t, s) in pinned[:2]:
+        ctx.distance(rule, v, t, None, s, prec)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for (v, t, s) in pinned:
+            ctx.distance(rule, v, t, None, s, prec)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * pairs_per_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(v.nbytes + t.nbytes for v, t, _ in pinned)),
+           "d2h_bytes_per_step": 8 * len(pinned),
+           "how": "wd_distance with pinned host mesh buffers, one synchronous call per query"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = pair_roofline_peak(sm_count, peaks.get("sm_max_mhz", 2032.0))
+    roof = {"bound": "alu", "achieved": pair_rate / 1e9, "peak": peak / 1e9, "unit": UNIT,
+            "frac": pair_rate / peak, "traffic": None,
+            "kernel": "pair_kernel (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
+            "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
+                          % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
+                             N_MUFU_PER_PAIR)}
+    if prec == wd.WD_FP64:
+        roof["note"] = "float64 path: bounded by the FP64 pipe, not by the FP32/MUFU roofline shown"
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(R, queries, args.cpu_sample_seconds)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == wd.WD_MIXED else "f64", "data": "synthetic",
+            "config": dict(cfg, pairs_per_step=pairs_per_step, queries_per_step=len(dq),
+                           parallelism="dp%d (independent replicas)" % world),
+            "queries_per_s": world * len(dq) * args.steps / total_s,
+            "query_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                 "max": lat[-1], "note": "per-query kernel time, back-to-back queries"},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "accuracy": accuracy, "distances": d_values[:len(dq)]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,416 @@
+// C ABI entry points: context, scratch, transforms and the distance.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "wd_internal.h"
+
+void wd_release_all_rules(wd_ctx* ctx);
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+bool host_mesh_ok(const wd_mesh* m, std::string* why)
+{
+    if (!m) { *why = "null mesh"; return false; }
+    if (m->n_verts < 0 || m->n_tris < 0) { *why = "negative mesh size"; return false; }
+    if ((m->n_verts > 0 && !m->verts) || (m->n_tris > 0 && !m->tris)) { *why = "null mesh array"; return false; }
+    if (m->n_tris > ((int64_t)1 << 31)) { *why = "too many triangles"; return false; }
+    for (int64_t i = 0; i < 3 * m->n_verts; ++i)
+        if (!std::isfinite(m->verts[i])) { *why = "non-finite vertex coordinate"; return false; }
+    for (int64_t i = 0; i < 3 * m->n_tris; ++i)
+        if (m->tris[i] < 0 || m->tris[i] >= m->n_verts) { *why = "triangle index out of range"; return false; }
+    return true;
+}
+
+wd_status check_common(wd_ctx* ctx, const wd_rule* rule, int precision)
+{
+    WD_CHECK(ctx && rule, WD_EINVAL, "null context or rule");
+    WD_CHECK(rule->ctx == ctx, WD_EINVAL, "rule belongs to another context");
+    WD_CHECK(precision == WD_FP64 || precision == WD_MIXED, WD_EINVAL, "precision must be WD_FP64 or WD_MIXED");
+    return WD_OK;
+}
+
+wd_status check_nu(const wd_measure* nu)
+{
+    WD_CHECK(nu, WD_EINVAL, "null reference measure");
+    if (nu->kind == WD_NU_SPHERE) {
+        WD_CHECK(std::isfinite(nu->radius) && nu->radius > 0.0, WD_EINVAL, "sphere radius must be finite and > 0");
+        for (int j = 0; j < 3; ++j)
+            WD_CHECK(std::isfinite(nu->center[j]), WD_EINVAL, "non-finite sphere center");
+        return WD_OK;
+    }
+    WD_CHECK(nu->kind == WD_NU_MESH, WD_EINVAL, "unknown reference-measure kind");
+    WD_CHECK(nu->mesh, WD_EINVAL, "WD_NU_MESH needs a mesh");
+    WD_CHECK(nu->mesh->n_verts >= 0 && nu->mesh->n_tris >= 0, WD_EINVAL, "negative mesh size");
+    return WD_OK;
+}
+
+// Layout of one pair evaluation inside the context scratch, from offset `base`.
+struct CoreLayout {
+    PairPlan plan;
+    size_t rec = 0, partial = 0, blockD = 0, end = 0;
+};
+
+CoreLayout core_layout(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, int64_t n_rec, size_t base)
+{
+    CoreLayout L;
+    wd_plan_pair(ctx, precision, mode, n_nodes, n_rec, &L.plan);
+    size_t off = align_up(base);
+    L.rec = off;
+    off += align_up((size_t)n_rec * wd_tri_record_bytes(precision));
+    L.partial = off;
+    if (L.plan.nchunks > 1) off += align_up((size_t)L.plan.nchunks * n_nodes * 2 * sizeof(double));
+    L.blockD = off;
+    off += align_up((size_t)(L.plan.n_nb > 0 ? L.plan.n_nb : 1) * sizeof(double));
+    L.end = off;
+    return L;
+}
+
+// Stage mu (and a mesh nu, negated) and run the pair kernel in `mode`.
+// Device pointers only; scratch must already hold `L.end` bytes.
+wd_status run_core(wd_ctx* ctx, wd_rule* rule, const CoreLayout& L, int precision, int mode,
+                   const double* d_verts, int64_t nv, const int32_t* d_tris, int64_t nt,
+                   const wd_measure* nu, double s, double* d_out, double* d_out_im, cudaStream_t st)
+{
+    void* rec = ctx->ws + L.rec;
+    wd_status r = wd_launch_stage(ctx, precision, d_verts, nv, d_tris, nt, 1.0, rec, 0, st);
+    if (r != WD_OK) return r;
+    PairArgs a;
+    a.xi = rule->d_xi;
+    a.n = rule->n_eval;
+    a.tris = rec;
+    a.T = L.plan.n_tris;
+    if (mode == MODE_DIST) {
+        if (nu->kind == WD_NU_MESH) {
+            r = wd_launch_stage(ctx, precision, nu->mesh->verts, nu->mesh->n_verts, nu->mesh->tris,
+                                nu->mesh->n_tris, -1.0, rec, nt, st);
+            if (r != WD_OK) return r;
+        } else {
+            r = wd_rule_sphere(ctx, rule, nu->radius, nu->center, &a.nu, st);
+            if (r != WD_OK) return r;
+        }
+        r = wd_rule_weights(ctx, rule, s, &a.W, st);
+        if (r != WD_OK) return r;
+    }
+    a.partial = reinterpret_cast<double*>(ctx->ws + L.partial);
+    a.cnt = ctx->d_counters;
+    a.blockD = reinterpret_cast<double*>(ctx->ws + L.blockD);
+    a.done = ctx->d_flags + 1;
+    a.out = d_out;
+    a.out_im = d_out_im;
+    if (L.plan.n_items == 0) {
+        // no nodes: D = 0, nothing to transform
+        if (mode == MODE_DIST) WD_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double), st));
+        return WD_OK;
+    }
+    return wd_launch_pair(ctx, precision, mode, L.plan, a, st);
+}
+
+wd_status finish_host(wd_ctx* ctx, cudaStream_t st)
+{
+    WD_CUDA(cudaStreamSynchronize(st));
+    int flag = 0;
+    WD_CUDA(cudaMemcpy(&flag, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        WD_CUDA(cudaMemset(ctx->d_flags, 0, sizeof(int)));
+        wd_set_error("invalid mesh input (index out of range or non-finite vertex)");
+        return WD_EINVAL;
+    }
+    return WD_OK;
+}
+
+wd_status upload_mesh(wd_ctx* ctx, const wd_mesh* m, size_t ov, size_t ot, cudaStream_t st)
+{
+    if (m->n_verts > 0)
+        WD_CUDA(cudaMemcpyAsync(ctx->ws + ov, m->verts, sizeof(double) * 3 * m->n_verts,
+                                cudaMemcpyHostToDevice, st));
+    if (m->n_tris > 0)
+        WD_CUDA(cudaMemcpyAsync(ctx->ws + ot, m->tris, sizeof(int32_t) * 3 * m->n_tris,
+                                cudaMemcpyHostToDevice, st));
+    return WD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ internals
+void wd_set_error(const std::string& msg) { g_last_error = msg; }
+
+wd_status wd_cuda_status(cudaError_t e, const char* what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return WD_ENOMEM;
+    }
+    return WD_ECUDA;
+}
+
+wd_status wd_activate(wd_ctx* ctx)
+{
+    WD_CUDA(cudaSetDevice(ctx->device));
+    return WD_OK;
+}
+
+wd_status wd_ws_reserve(wd_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_bytes) return WD_OK;
+    size_t want = bytes + bytes / 4;
+    WD_CUDA(cudaDeviceSynchronize());
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        wd_set_error("out of device memory for scratch (" + std::to_string(want) + " bytes)");
+        return WD_ENOMEM;
+    }
+    ctx->ws_bytes = want;
+    return WD_OK;
+}
+
+wd_status wd_counters_reserve(wd_ctx* ctx, int64_t n)
+{
+    if (n <= ctx->n_counters) return WD_OK;
+    int64_t want = n + n / 4 + 64;
+    WD_CUDA(cudaDeviceSynchronize());
+    cudaFree(ctx->d_counters);
+    ctx->d_counters = nullptr;
+    ctx->n_counters = 0;
+    if (cudaMalloc(&ctx->d_counters, sizeof(int) * want) != cudaSuccess) {
+        cudaGetLastError();
+        wd_set_error("out of device memory for completion counters");
+        return WD_ENOMEM;
+    }
+    WD_CUDA(cudaMemset(ctx->d_counters, 0, sizeof(int) * want));
+    ctx->n_counters = want;
+    return WD_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" const char* wd_last_error(const wd_ctx*) { return g_last_error.c_str(); }
+
+extern "C" wd_status wd_create(int device, wd_ctx** out)
+{
+    WD_CHECK(out, WD_EINVAL, "null output pointer");
+    *out = nullptr;
+    int count = 0;
+    WD_CUDA(cudaGetDeviceCount(&count));
+    WD_CHECK(device >= 0 && device < count, WD_EINVAL, "no such CUDA device");
+    WD_CUDA(cudaSetDevice(device));
+    wd_ctx* c = new wd_ctx();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scalar, 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        wd_status st = wd_cuda_status(e, "wd_create");
+        cudaFree(c->d_flags);
+        cudaFree(c->d_scalar);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return WD_OK;
+}
+
+extern "C" void wd_destroy(wd_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    wd_release_all_rules(ctx);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_flags);
+    cudaFree(ctx->d_scalar);
+    delete ctx;
+}
+
+extern "C" int64_t wd_launch_count(const wd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" wd_status wd_sync(wd_ctx* ctx, void* stream)
+{
+    WD_CHECK(ctx, WD_EINVAL, "null context");
+    wd_status st = wd_activate(ctx);
+    if (st != WD_OK) return st;
+    return finish_host(ctx, (cudaStream_t)stream);
+}
+
+// ---- transforms
+extern "C" wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
+                                    int64_t nv, const int32_t* d_tris, int64_t nt, int precision,
+                                    double* d_re, double* d_im, void* stream)
+{
+    wd_status st = check_common(ctx, rule_c, precision);
+    if (st != WD_OK) return st;
+    WD_CHECK(nv >= 0 && nt >= 0 && nt <= ((int64_t)1 << 31), WD_EINVAL, "mesh size out of range");
+    WD_CHECK((nt == 0 || (d_verts && d_tris)) && (rule_c->n_eval == 0 || (d_re && d_im)),
+             WD_EINVAL, "null device pointer");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    wd_rule* rule = const_cast<wd_rule*>(rule_c);
+    cudaStream_t s = (cudaStream_t)stream;
+    CoreLayout L = core_layout(ctx, precision, MODE_FT, rule->n_eval, nt, 0);
+    if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
+    if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
+    return run_core(ctx, rule, L, precision, MODE_FT, d_verts, nv, d_tris, nt, nullptr, 0.0, d_re, d_im, s);
+}
+
+extern "C" wd_status wd_mesh_ft(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mesh, int precision,
+                                double* out_re, double* out_im)
+{
+    wd_status st = check_common(ctx, rule_c, precision);
+    if (st != WD_OK) return st;
+    std::string why;
+    WD_CHECK(host_mesh_ok(mesh, &why), WD_EINVAL, why);
+    const int64_t n = rule_c->n_eval;
+    WD_CHECK(n == 0 || (out_re && out_im), WD_EINVAL, "null output array");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    wd_rule* rule = const_cast<wd_rule*>(rule_c);
+    size_t ov = 0, ot = align_up(sizeof(double) * 3 * mesh->n_verts);
+    size_t oo = ot + align_up(sizeof(int32_t) * 3 * mesh->n_tris);
+    size_t base = oo + 2 * align_up(sizeof(double) * n);
+    CoreLayout L = core_layout(ctx, precision, MODE_FT, n, mesh->n_tris, base);
+    if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
+    if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
+    cudaStream_t s = 0;
+    if ((st = upload_mesh(ctx, mesh, ov, ot, s)) != WD_OK) return st;
+    double* d_re = reinterpret_cast<double*>(ctx->ws + oo);
+    double* d_im = reinterpret_cast<double*>(ctx->ws + oo + align_up(sizeof(double) * n));
+    st = run_core(ctx, rule, L, precision, MODE_FT, reinterpret_cast<const double*>(ctx->ws + ov),
+                  mesh->n_verts, reinterpret_cast<const int32_t*>(ctx->ws + ot), mesh->n_tris, nullptr,
+                  0.0, d_re, d_im, s);
+    if (st != WD_OK) return st;
+    if (n > 0) {
+        WD_CUDA(cudaMemcpyAsync(out_re, d_re, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        WD_CUDA(cudaMemcpyAsync(out_im, d_im, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
+    return finish_host(ctx, s);
+}
+
+extern "C" wd_status wd_sphere_ft_dev(wd_ctx* ctx, const wd_rule* rule, double radius, const double center[3],
+                                      double* d_re, double* d_im, void* stream)
+{
+    wd_status st = check_common(ctx, rule, WD_FP64);
+    if (st != WD_OK) return st;
+    WD_CHECK(center, WD_EINVAL, "null center");
+    WD_CHECK(std::isfinite(radius) && radius > 0.0, WD_EINVAL, "radius must be finite and > 0");
+    for (int j = 0; j < 3; ++j) WD_CHECK(std::isfinite(center[j]), WD_EINVAL, "non-finite center");
+    WD_CHECK(rule->n_eval == 0 || (d_re && d_im), WD_EINVAL, "null device pointer");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    return wd_launch_sphere(ctx, rule->d_xi, rule->n_eval, radius, center, d_re, d_im, nullptr,
+                            (cudaStream_t)stream);
+}
+
+extern "C" wd_status wd_sphere_ft(wd_ctx* ctx, const wd_rule* rule, double radius, const double center[3],
+                                  double* out_re, double* out_im)
+{
+    wd_status st = check_common(ctx, rule, WD_FP64);
+    if (st != WD_OK) return st;
+    const int64_t n = rule->n_eval;
+    WD_CHECK(n == 0 || (out_re && out_im), WD_EINVAL, "null output array");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if ((st = wd_ws_reserve(ctx, 2 * align_up(sizeof(double) * (n > 0 ? n : 1)))) != WD_OK) return st;
+    double* d_re = reinterpret_cast<double*>(ctx->ws);
+    double* d_im = reinterpret_cast<double*>(ctx->ws + align_up(sizeof(double) * (n > 0 ? n : 1)));
+    st = wd_sphere_ft_dev(ctx, rule, radius, center, d_re, d_im, nullptr);
+    if (st != WD_OK) return st;
+    if (n > 0) {
+        WD_CUDA(cudaMemcpy(out_re, d_re, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        WD_CUDA(cudaMemcpy(out_im, d_im, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    }
+    return finish_host(ctx, 0);
+}
+
+// ---- distance
+extern "C" wd_status wd_distance_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
+                                     int64_t nv, const int32_t* d_tris, int64_t nt, const wd_measure* nu,
+                                     double s, int precision, double* d_dist2, void* stream)
+{
+    wd_status st = check_common(ctx, rule_c, precision);
+    if (st != WD_OK) return st;
+    if ((st = check_nu(nu)) != WD_OK) return st;
+    WD_CHECK(std::isfinite(s) && s > 0.0, WD_EINVAL, "s must be finite and > 0");
+    WD_CHECK(nv >= 0 && nt >= 0, WD_EINVAL, "negative mesh size");
+    WD_CHECK((nt == 0 || (d_verts && d_tris)) && d_dist2, WD_EINVAL, "null device pointer");
+    const int64_t nt2 = nu->kind == WD_NU_MESH ? nu->mesh->n_tris : 0;
+    WD_CHECK(nt + nt2 <= ((int64_t)1 << 31), WD_EINVAL, "too many triangles");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    wd_rule* rule = const_cast<wd_rule*>(rule_c);
+    CoreLayout L = core_layout(ctx, precision, MODE_DIST, rule->n_eval, nt + nt2, 0);
+    if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
+    if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
+    return run_core(ctx, rule, L, precision, MODE_DIST, d_verts, nv, d_tris, nt, nu, s, d_dist2, nullptr,
+                    (cudaStream_t)stream);
+}
+
+extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mu, const wd_measure* nu,
+                                 double s, int precision, double* dist2)
+{
+    wd_status st = check_common(ctx, rule_c, precision);
+    if (st != WD_OK) return st;
+    if ((st = check_nu(nu)) != WD_OK) return st;
+    WD_CHECK(std::isfinite(s) && s > 0.0, WD_EINVAL, "s must be finite and > 0");
+    WD_CHECK(dist2, WD_EINVAL, "null output");
+    std::string why;
+    WD_CHECK(host_mesh_ok(mu, &why), WD_EINVAL, why);
+    if (nu->kind == WD_NU_MESH) WD_CHECK(host_mesh_ok(nu->mesh, &why), WD_EINVAL, "reference mesh: " + why);
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    wd_rule* rule = const_cast<wd_rule*>(rule_c);
+    const wd_mesh* m2 = nu->kind == WD_NU_MESH ? nu->mesh : nullptr;
+    const int64_t nt2 = m2 ? m2->n_tris : 0;
+    size_t ov = 0, ot = align_up(sizeof(double) * 3 * mu->n_verts);
+    size_t ov2 = ot + align_up(sizeof(int32_t) * 3 * mu->n_tris);
+    size_t ot2 = ov2 + (m2 ? align_up(sizeof(double) * 3 * m2->n_verts) : 0);
+    size_t base = ot2 + (m2 ? align_up(sizeof(int32_t) * 3 * m2->n_tris) : 0);
+    CoreLayout L = core_layout(ctx, precision, MODE_DIST, rule->n_eval, mu->n_tris + nt2, base);
+    if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
+    if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
+    cudaStream_t strm = 0;
+    if ((st = upload_mesh(ctx, mu, ov, ot, strm)) != WD_OK) return st;
+    wd_mesh dm2{};
+    wd_measure dnu = *nu;
+    if (m2) {
+        if ((st = upload_mesh(ctx, m2, ov2, ot2, strm)) != WD_OK) return st;
+        dm2.verts = reinterpret_cast<const double*>(ctx->ws + ov2);
+        dm2.n_verts = m2->n_verts;
+        dm2.tris = reinterpret_cast<const int32_t*>(ctx->ws + ot2);
+        dm2.n_tris = m2->n_tris;
+        dnu.mesh = &dm2;
+    }
+    st = run_core(ctx, rule, L, precision, MODE_DIST, reinterpret_cast<const double*>(ctx->ws + ov),
+                  mu->n_verts, reinterpret_cast<const int32_t*>(ctx->ws + ot), mu->n_tris, &dnu, s,
+                  ctx->d_scalar, nullptr, strm);
+    if (st != WD_OK) return st;
+    WD_CUDA(cudaMemcpyAsync(dist2, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, strm));
+    return finish_host(ctx, strm);
+}
+
+extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule, const double*, int64_t,
+                                          const int32_t*, int64_t, const wd_measure*, double, int,
+                                          double*, double*, void*)
+{
+    wd_status st = check_common(ctx, rule, WD_FP64);
+    if (st != WD_OK) return st;
+    wd_set_error("wd_distance_grad_dev: not available in this build");
+    return WD_EINVAL;
+}
+
+extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule, const wd_mesh*, const wd_measure*,
+                                      double, int, double*, double*)
+{
+    wd_status st = check_common(ctx, rule, WD_FP64);
+    if (st != WD_OK) return st;
+    wd_set_error("wd_distance_grad: not available in this build");
+    return WD_EINVAL;
+}

@@ -1,0 +1,142 @@
+// Internal declarations shared by the libwd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wd.h"
+
+// ------------------------------------------------------------------ errors
+void wd_set_error(const std::string& msg);
+wd_status wd_cuda_status(cudaError_t e, const char* what);
+
+#define WD_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return wd_cuda_status(e__, #call); \
+    } while (0)
+
+#define WD_CHECK(cond, code, msg)       \
+    do {                                \
+        if (!(cond)) {                  \
+            wd_set_error(msg);          \
+            return (code);              \
+        }                               \
+    } while (0)
+
+// ------------------------------------------------------------------ records
+// One triangle as the float64 pair kernel reads it (80 bytes).
+struct __align__(16) TriRecD {
+    double m[3];   // centroid
+    double e1[3];  // b - a
+    double e2[3];  // c - a
+    double gam;    // |(b - a) x (c - a)| = twice the area (negative for a subtracted mesh)
+};
+
+// One triangle as the mixed pair kernel reads it (64 bytes).
+struct __align__(16) TriRecF {
+    float mh[3];   // centroid, high float32 part
+    float ml[3];   // centroid - high part, as float32
+    float e1[3];
+    float e2[3];
+    float gam;     // twice the area, high float32 part (negative for a subtracted mesh)
+    float gam_lo;  // remainder of gam
+    float pad[2];
+};
+
+// ------------------------------------------------------------------ rule
+struct wd_rule {
+    wd_ctx* ctx = nullptr;
+    wd_rule_desc desc{};
+    bool cached = false;              // owned by the context's descriptor cache
+    int64_t n_eval = 0, n_total = 0;
+    std::vector<double> h_xi;         // SoA, 3 * n_eval
+    std::vector<double> h_wg;         // s-free weights
+    double* d_xi = nullptr;           // SoA on the device
+    double* d_wg = nullptr;
+    std::map<double, double*> w_cache;                  // s -> W_k
+    std::map<std::array<double, 4>, double*> nu_cache;  // (radius, center) -> nu^ (re, im interleaved)
+};
+
+// ------------------------------------------------------------------ context
+struct wd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::recursive_mutex mu;
+    std::vector<wd_rule*> rules;      // descriptor cache
+    std::vector<wd_rule*> explicit_rules;
+    // growable scratch
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    // per-node-block completion counters (self-resetting) and the flags word
+    int* d_counters = nullptr;
+    int64_t n_counters = 0;
+    int* d_flags = nullptr;           // [0]: invalid-input flag, [1]: final-block counter
+    double* d_scalar = nullptr;       // staging for host-variant scalar results
+    int64_t launches = 0;
+};
+
+// make ctx's device current
+wd_status wd_activate(wd_ctx* ctx);
+// grow the scratch area to at least `bytes`
+wd_status wd_ws_reserve(wd_ctx* ctx, size_t bytes);
+wd_status wd_counters_reserve(wd_ctx* ctx, int64_t n);
+
+// cached per-rule device arrays
+wd_status wd_rule_weights(wd_ctx* ctx, wd_rule* rule, double s, const double** d_w, cudaStream_t st);
+wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double* center,
+                         const double** d_nu, cudaStream_t st);
+
+// ------------------------------------------------------------------ kernels
+enum PairMode { MODE_DIST = 0, MODE_FT = 1 };
+
+struct PairPlan {
+    int64_t n_nodes = 0;
+    int64_t n_tris = 0;       // records (mu and, for a mesh nu, its negated triangles)
+    int64_t n_nb = 0;         // node blocks
+    int64_t n_tiles = 0;
+    int tiles_per_chunk = 0;
+    int nchunks = 0;
+    int64_t n_items = 0;
+    int grid = 0;
+};
+
+struct PairArgs {
+    const double* xi = nullptr;   // SoA nodes
+    int64_t n = 0;
+    const void* tris = nullptr;   // TriRecD or TriRecF
+    int64_t T = 0;
+    const double* W = nullptr;    // MODE_DIST: weights
+    const double* nu = nullptr;   // MODE_DIST: sphere nu^ (re, im) or null
+    double* partial = nullptr;    // nchunks * n * 2 when nchunks > 1
+    int* cnt = nullptr;           // n_nb counters
+    double* blockD = nullptr;     // n_nb partial sums
+    int* done = nullptr;          // final-block counter
+    double* out = nullptr;        // MODE_DIST: D; MODE_FT: re[n]
+    double* out_im = nullptr;     // MODE_FT: im[n]
+};
+
+constexpr int WD_NPB = 256;   // nodes per block: one node per thread
+constexpr int WD_TILE = 128;  // triangles per shared-memory tile
+
+size_t wd_tri_record_bytes(int precision);
+// stage triangles (a1): records for mu (sign +1) at offset 0 and optionally a
+// second mesh (sign -1) after them
+wd_status wd_launch_stage(wd_ctx* ctx, int precision, const double* d_verts, int64_t nv,
+                          const int32_t* d_tris, int64_t nt, double sign, void* d_rec,
+                          int64_t rec_offset, cudaStream_t st);
+wd_status wd_plan_pair(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, int64_t n_tris,
+                       PairPlan* plan);
+wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
+                         const PairArgs& args, cudaStream_t st);
+wd_status wd_launch_sphere(wd_ctx* ctx, const double* d_xi, int64_t n, double radius,
+                           const double* center, double* d_re, double* d_im, double* d_inter,
+                           cudaStream_t st);
+wd_status wd_launch_weights(wd_ctx* ctx, const double* d_xi, const double* d_wg, int64_t n,
+                            double s, double* d_w, cudaStream_t st);

@@ -1,0 +1,575 @@
+// Mesh staging and the (triangle, frequency-node) pair kernels.
+//
+// For a triangle T with vertices a, b, c and a node xi, the transform of the
+// surface measure (Eq. (simplex32_ft), angular convention) is
+//     F_T(xi) = gamma * G[t_a, t_b, t_c],  G(t) = -exp(-i t),  t_v = xi.v,
+// the second divided difference of G times gamma = |(b - a) x (c - a)|.
+// With the centroid phase t_m = xi.m, the edge gaps g1 = xi.(b - a),
+// g2 = xi.(c - a), g3 = g2 - g1 and the centred phases
+//     y_a = -(g1 + g2)/3,  y_b = (2 g1 - g2)/3,  y_c = (2 g2 - g1)/3,
+// two evaluations are used:
+//   * all gaps below DELTA: the Taylor series about t_m,
+//       G = exp(-i t_m) sum_n (-i)^n h_n(y_a, y_b, y_c) / (n + 2)!,
+//     where, because y_a + y_b + y_c = 0, the complete homogeneous symmetric
+//     polynomials satisfy h_n = p h_{n-2} + q h_{n-3} with
+//     p = (g1^2 - g1 g2 + g2^2)/3 and q = y_a y_b y_c (h_0 = 1, h_1 = 0);
+//   * otherwise the divided-difference recurrence over the pair (x, z) with
+//     the largest gap D = t_z - t_x and the middle node w,
+//       G = (G[t_w, t_z] - G[t_x, t_w]) / D,
+//       G[u, v] = i exp(-i (u + v)/2) sinc((v - u)/2),
+//     each first-order term being exact and cancellation-free, so the only
+//     cancellation is the final difference, bounded by the machine epsilon
+//     over D >= DELTA.
+// Per node the transforms are summed over all triangles (linearity,
+// Sec. 3.1); the distance epilogue subtracts nu^, weights by
+// w_k (1 + |xi_k|^2)^(-s) and reduces (the quadrature of Eq. (sobolev_2)).
+#include <cstdint>
+#include <type_traits>
+
+#include "wd_internal.h"
+
+namespace {
+
+// ------------------------------------------------------------------ staging (a1)
+template <bool MIXED>
+__global__ void stage_kernel(const double* __restrict__ verts, int64_t nv,
+                             const int32_t* __restrict__ tris, int64_t nt, double sign,
+                             void* __restrict__ rec_out, int* __restrict__ flags)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
+        bool ok = ia >= 0 && ia < nv && ib >= 0 && ib < nv && ic >= 0 && ic < nv;
+        double a[3] = {0, 0, 0}, b[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+        if (ok) {
+            for (int j = 0; j < 3; ++j) {
+                a[j] = verts[3 * ia + j];
+                b[j] = verts[3 * ib + j];
+                c[j] = verts[3 * ic + j];
+                ok = ok && isfinite(a[j]) && isfinite(b[j]) && isfinite(c[j]);
+            }
+        }
+        if (!ok) {
+            atomicOr(&flags[0], 1);
+            for (int j = 0; j < 3; ++j) a[j] = b[j] = c[j] = 0.0;
+        }
+        double m[3], e1[3], e2[3];
+        for (int j = 0; j < 3; ++j) {
+            m[j] = (a[j] + b[j] + c[j]) * (1.0 / 3.0);
+            e1[j] = b[j] - a[j];
+            e2[j] = c[j] - a[j];
+        }
+        const double nx = e1[1] * e2[2] - e1[2] * e2[1];
+        const double ny = e1[2] * e2[0] - e1[0] * e2[2];
+        const double nz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double gam = sign * sqrt(nx * nx + ny * ny + nz * nz);
+        if (MIXED) {
+            TriRecF r;
+            for (int j = 0; j < 3; ++j) {
+                r.mh[j] = (float)m[j];
+                r.ml[j] = (float)(m[j] - (double)r.mh[j]);
+                r.e1[j] = (float)e1[j];
+                r.e2[j] = (float)e2[j];
+            }
+            r.gam = (float)gam;
+            r.gam_lo = (float)(gam - (double)r.gam);
+            r.pad[0] = r.pad[1] = 0.0f;
+            static_cast<TriRecF*>(rec_out)[t] = r;
+        } else {
+            TriRecD r;
+            for (int j = 0; j < 3; ++j) {
+                r.m[j] = m[j];
+                r.e1[j] = e1[j];
+                r.e2[j] = e2[j];
+            }
+            r.gam = gam;
+            static_cast<TriRecD*>(rec_out)[t] = r;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ shared pieces
+// Taylor branch bounds: below a largest gap DELTA the centred phases satisfy
+// |y| <= 2 DELTA / 3. float64: DELTA = 1, series to n = 18 (remainder < 1e-18);
+// mixed: DELTA = 1.5, series to n = 13 (|y| <= 1, remainder < 1e-10).
+constexpr double kDelta64 = 1.0;
+constexpr int kTerms64 = 18;
+constexpr float kDelta32 = 1.5f;
+constexpr int kTerms32 = 13;
+
+// 1/(n+2)! for n = 0..22
+__device__ constexpr double kInvFact2[23] = {
+    1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
+    1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0, 1.0 / 87178291200.0,
+    1.0 / 1307674368000.0, 1.0 / 20922789888000.0, 1.0 / 355687428096000.0,
+    1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0, 1.0 / 2432902008176640000.0,
+    1.0 / 51090942171709440000.0, 1.0 / 1124000727777607680000.0,
+    1.0 / 25852016738884976640000.0, 1.0 / 620448401733239439360000.0};
+
+// sum_n (-i)^n h_n / (n+2)! with h_n = p h_{n-2} + q h_{n-3}
+template <typename Real, int NT>
+__device__ __forceinline__ void taylor_sum(Real p, Real q, Real& sr, Real& si)
+{
+    Real h[NT + 1];
+    h[0] = Real(1);
+    if (NT >= 1) h[1] = Real(0);
+    if (NT >= 2) h[2] = p;
+    if (NT >= 3) h[3] = q;
+#pragma unroll
+    for (int n = 4; n <= NT; ++n) h[n] = p * h[n - 2] + q * h[n - 3];
+    sr = Real(0);
+    si = Real(0);
+#pragma unroll
+    for (int n = NT; n >= 0; --n) {
+        // (-i)^n: 1, -i, -1, i
+        const Real c = Real(kInvFact2[n]);
+        switch (n & 3) {
+        case 0: sr += c * h[n]; break;
+        case 1: si -= c * h[n]; break;
+        case 2: sr -= c * h[n]; break;
+        default: si += c * h[n]; break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ float64 pair (a3, a4)
+__device__ __forceinline__ double sinc64(double x)
+{
+    return x == 0.0 ? 1.0 : sin(x) / x;
+}
+
+struct NodeD {
+    double x, y, z;
+};
+
+__device__ __forceinline__ void pair_f64(const NodeD& q, const TriRecD& t, double& fr, double& fi)
+{
+    const double tm = fma(q.x, t.m[0], fma(q.y, t.m[1], q.z * t.m[2]));
+    const double g1 = fma(q.x, t.e1[0], fma(q.y, t.e1[1], q.z * t.e1[2]));
+    const double g2 = fma(q.x, t.e2[0], fma(q.y, t.e2[1], q.z * t.e2[2]));
+    const double g3 = g2 - g1;
+    const double a1 = fabs(g1), a2 = fabs(g2), a3 = fabs(g3);
+    const double gmax = fmax(a1, fmax(a2, a3));
+    const double ya = -(g1 + g2) * (1.0 / 3.0);
+    const double yb = (2.0 * g1 - g2) * (1.0 / 3.0);
+    const double yc = (2.0 * g2 - g1) * (1.0 / 3.0);
+    double gr, gi;
+    if (gmax < kDelta64) {
+        const double p = (g1 * g1 - g1 * g2 + g2 * g2) * (1.0 / 3.0);
+        const double qq = ya * yb * yc;
+        double sr, si;
+        taylor_sum<double, kTerms64>(p, qq, sr, si);
+        double s, c;
+        sincos(tm, &s, &c);
+        // exp(-i tm) (sr + i si)
+        gr = c * sr + s * si;
+        gi = c * si - s * sr;
+    } else {
+        // largest gap: A = (a, c) with g2, B = (a, b) with g1, C = (b, c) with g3;
+        // P is the first-order term on the far side, Q on the near side.
+        // Edge midpoints relative to the centroid: (a+b)/2 -> -y_c/2,
+        // (b+c)/2 -> -y_a/2, (a+c)/2 -> -y_b/2.
+        const bool caseA = (a2 >= a1) && (a2 >= a3);
+        const bool caseB = !caseA && (a1 >= a3);
+        const bool caseC = !caseA && !caseB;
+        const double offP = caseC ? -0.5 * yb : -0.5 * ya;  // C: (a,c) ; A, B: (b,c)
+        const double hP = caseC ? 0.5 * g2 : 0.5 * g3;
+        const double offQ = caseB ? -0.5 * yb : -0.5 * yc;  // B: (a,c) ; A, C: (a,b)
+        const double hQ = caseB ? 0.5 * g2 : 0.5 * g1;
+        const double D = caseA ? g2 : (caseB ? g1 : g3);
+        double sP, cP, sQ, cQ;
+        sincos(tm + offP, &sP, &cP);
+        sincos(tm + offQ, &sQ, &cQ);
+        const double scP = sinc64(hP), scQ = sinc64(hQ);
+        // S_P - S_Q with S = exp(-i theta) sinc(h); G = i (S_P - S_Q) / D
+        const double dr = cP * scP - cQ * scQ;
+        const double di = sQ * scQ - sP * scP;
+        gr = -di / D;
+        gi = dr / D;
+    }
+    fr = t.gam * gr;
+    fi = t.gam * gi;
+}
+
+// ------------------------------------------------------------------ mixed pair
+struct NodeF {
+    float x, y, z;     // xi (radians), float32
+    float hx, hy, hz;  // xi / 2 pi, high float32 part
+    float lx, ly, lz;  // xi / 2 pi - high part
+};
+
+// sin(x)/x: reduction by the nearest multiple of pi (two-constant split) and
+// the Taylor polynomial of sin(r)/r on |r| <= pi/2 (remainder < 5e-10).
+__device__ __forceinline__ float sinc32(float x)
+{
+    const float k = rintf(x * 0.318309886183790672f);
+    float r = fmaf(-k, 3.14159274101257324f, x);
+    r = fmaf(-k, -8.74227766e-8f, r);
+    const float r2 = r * r;
+    float P = -1.0f / 1307674368000.0f;
+    P = fmaf(P, r2, 1.0f / 6227020800.0f);
+    P = fmaf(P, r2, -1.0f / 39916800.0f);
+    P = fmaf(P, r2, 1.0f / 362880.0f);
+    P = fmaf(P, r2, -1.0f / 5040.0f);
+    P = fmaf(P, r2, 1.0f / 120.0f);
+    P = fmaf(P, r2, -1.0f / 6.0f);
+    P = fmaf(P, r2, 1.0f);
+    // sin(x) = (-1)^k r P; for k = 0, r == x exactly
+    const float half = 0.5f * k;
+    const float sgn = (half == rintf(half)) ? 1.0f : -1.0f;
+    const float qf = (k == 0.0f) ? 1.0f : __fdividef(sgn * r, x);
+    return P * qf;
+}
+
+// exp(-i 2 pi tau) for tau in turns, without rounding 2 pi into the argument:
+// reduction to the nearest quarter turn (exact), x = 2 pi u carried as a float
+// pair, Taylor polynomials of sin and cos on |x| <= pi/4 (remainders below
+// 2e-9), and a quarter-turn rotation by selects.
+__device__ __forceinline__ void expm_turns(float tau, float& er, float& ei)
+{
+    const float k = rintf(4.0f * tau);
+    const float u = fmaf(-0.25f, k, tau);  // exact, |u| <= 1/8
+    const float xh = u * 6.28318548202514648f;
+    float xl = fmaf(u, 6.28318548202514648f, -xh);
+    xl = fmaf(u, -1.74845553e-7f, xl);     // 2 pi - float(2 pi)
+    const float x2 = xh * xh;
+    float ps = 1.0f / 362880.0f;
+    ps = fmaf(ps, x2, -1.0f / 5040.0f);
+    ps = fmaf(ps, x2, 1.0f / 120.0f);
+    ps = fmaf(ps, x2, -1.0f / 6.0f);
+    const float sn = xh + fmaf(xh * x2, ps, xl);
+    float pc = -1.0f / 3628800.0f;
+    pc = fmaf(pc, x2, 1.0f / 40320.0f);
+    pc = fmaf(pc, x2, -1.0f / 720.0f);
+    pc = fmaf(pc, x2, 1.0f / 24.0f);
+    const float cs = 1.0f + fmaf(x2 * x2, pc, fmaf(-0.5f, x2, -xh * xl));
+    // rotate by k quarter turns; k4 = k mod 4 in {-2, -1, 0, 1, 2}
+    const float k4 = fmaf(-4.0f, rintf(0.25f * k), k);
+    const bool sw = fabsf(k4) == 1.0f;
+    const float a = sw ? cs : sn;
+    const float b = sw ? sn : cs;
+    const float sin_t = (k4 < 0.0f || k4 > 1.5f) ? -a : a;
+    const float cos_t = (k4 > 0.5f || k4 < -1.5f) ? -b : b;
+    er = cos_t;  // exp(-i theta) = cos theta - i sin theta
+    ei = -sin_t;
+}
+
+__device__ __forceinline__ void pair_mixed(const NodeF& q, const TriRecF& t, float& fr, float& fi)
+{
+    // centroid phase in turns: exact high products reduced mod 1, plus the low terms
+    const float p0 = q.hx * t.mh[0], p1 = q.hy * t.mh[1], p2 = q.hz * t.mh[2];
+    const float r0 = fmaf(q.hx, t.mh[0], -p0);
+    const float r1 = fmaf(q.hy, t.mh[1], -p1);
+    const float r2 = fmaf(q.hz, t.mh[2], -p2);
+    float f = (p0 - rintf(p0)) + (p1 - rintf(p1));
+    f -= rintf(f);
+    f += p2 - rintf(p2);
+    f -= rintf(f);
+    float lo = r0 + r1 + r2;
+    lo = fmaf(q.hx, t.ml[0], lo);
+    lo = fmaf(q.hy, t.ml[1], lo);
+    lo = fmaf(q.hz, t.ml[2], lo);
+    lo = fmaf(q.lx, t.mh[0], lo);
+    lo = fmaf(q.ly, t.mh[1], lo);
+    lo = fmaf(q.lz, t.mh[2], lo);
+    const float tau = f + lo;  // turns
+    const float g1 = fmaf(q.x, t.e1[0], fmaf(q.y, t.e1[1], q.z * t.e1[2]));
+    const float g2 = fmaf(q.x, t.e2[0], fmaf(q.y, t.e2[1], q.z * t.e2[2]));
+    const float g3 = g2 - g1;
+    const float a1 = fabsf(g1), a2 = fabsf(g2), a3 = fabsf(g3);
+    const float gmax = fmaxf(a1, fmaxf(a2, a3));
+    const float ya = -(g1 + g2) * (1.0f / 3.0f);
+    const float yb = (2.0f * g1 - g2) * (1.0f / 3.0f);
+    const float yc = (2.0f * g2 - g1) * (1.0f / 3.0f);
+    float gr, gi;
+    if (gmax < kDelta32) {
+        const float p = (g1 * g1 - g1 * g2 + g2 * g2) * (1.0f / 3.0f);
+        const float qq = ya * yb * yc;
+        float sr, si;
+        taylor_sum<float, kTerms32>(p, qq, sr, si);
+        float c, s;
+        expm_turns(tau, c, s);  // (c, s) = exp(-i t_m)
+        gr = c * sr - s * si;
+        gi = c * si + s * sr;
+    } else {
+        const bool caseA = (a2 >= a1) && (a2 >= a3);
+        const bool caseB = !caseA && (a1 >= a3);
+        const bool caseC = !caseA && !caseB;
+        const float inv4pi = 0.0795774715459476679f;  // offsets -y/2 in turns: -y/(4 pi)
+        const float offP = caseC ? -inv4pi * yb : -inv4pi * ya;
+        const float hP = caseC ? 0.5f * g2 : 0.5f * g3;
+        const float offQ = caseB ? -inv4pi * yb : -inv4pi * yc;
+        const float hQ = caseB ? 0.5f * g2 : 0.5f * g1;
+        const float D = caseA ? g2 : (caseB ? g1 : g3);
+        float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
+        expm_turns(tau + offP, cP, sP);
+        expm_turns(tau + offQ, cQ, sQ);
+        const float scP = sinc32(hP), scQ = sinc32(hQ);
+        // S_P - S_Q, G = i (S_P - S_Q) / D
+        const float dr = cP * scP - cQ * scQ;
+        const float di = sP * scP - sQ * scQ;
+        const float inv = 1.0f / D;
+        gr = -di * inv;
+        gi = dr * inv;
+    }
+    // gamma carried as a float pair: its rounding is identical for congruent triangles
+    fr = fmaf(t.gam, gr, t.gam_lo * gr);
+    fi = fmaf(t.gam, gi, t.gam_lo * gi);
+}
+
+// Kahan-compensated float32 accumulation: the per-tile sum of nearly equal
+// terms at low frequency would otherwise round the same way at neighbouring
+// nodes, a coherent error that the mesh-minus-sphere difference magnifies.
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// ------------------------------------------------------------------ block reduction
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in warp 0
+}
+
+// ------------------------------------------------------------------ pair kernel (a3..a7)
+template <bool MIXED, int MODE>
+__global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const PairPlan p)
+{
+    using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
+    __shared__ __align__(16) Rec tile[WD_TILE];
+    __shared__ double red[WD_NPB / 32];
+    __shared__ int s_last;
+
+    const int64_t n = a.n;
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const int64_t nb = item / p.nchunks;
+        const int chunk = (int)(item - nb * p.nchunks);
+        const int64_t node = nb * WD_NPB + threadIdx.x;
+        const bool active = node < n;
+        const double x = active ? a.xi[node] : 0.0;
+        const double y = active ? a.xi[n + node] : 0.0;
+        const double z = active ? a.xi[2 * n + node] : 0.0;
+
+        double acc_r = 0.0, acc_i = 0.0;
+        NodeD qd{x, y, z};
+        NodeF qf;
+        if (MIXED) {
+            const double inv2pi = 0.15915494309189533576888376337251;
+            const double X = x * inv2pi, Y = y * inv2pi, Z = z * inv2pi;
+            qf.x = (float)x;
+            qf.y = (float)y;
+            qf.z = (float)z;
+            qf.hx = (float)X;
+            qf.hy = (float)Y;
+            qf.hz = (float)Z;
+            qf.lx = (float)(X - (double)qf.hx);
+            qf.ly = (float)(Y - (double)qf.hy);
+            qf.lz = (float)(Z - (double)qf.hz);
+        }
+        const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
+        int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
+        if (t1 > a.T) t1 = a.T;
+        for (int64_t tb = t0; tb < t1; tb += WD_TILE) {
+            const int cnt = (int)((t1 - tb) < WD_TILE ? (t1 - tb) : WD_TILE);
+            __syncthreads();
+            {
+                const uint4* src = reinterpret_cast<const uint4*>(static_cast<const Rec*>(a.tris) + tb);
+                uint4* dst = reinterpret_cast<uint4*>(tile);
+                const int nvec = cnt * (int)(sizeof(Rec) / 16);
+                for (int i = threadIdx.x; i < nvec; i += WD_NPB) dst[i] = __ldg(src + i);
+            }
+            __syncthreads();
+            if (MIXED) {
+                Kahan kr, ki;
+#pragma unroll 2
+                for (int j = 0; j < cnt; ++j) {
+                    float fr, fi;
+                    pair_mixed(qf, reinterpret_cast<const TriRecF*>(tile)[j], fr, fi);
+                    kr.add(fr);
+                    ki.add(fi);
+                }
+                acc_r += kr.value();
+                acc_i += ki.value();
+            } else {
+                for (int j = 0; j < cnt; ++j) {
+                    double fr, fi;
+                    pair_f64(qd, reinterpret_cast<const TriRecD*>(tile)[j], fr, fi);
+                    acc_r += fr;
+                    acc_i += fi;
+                }
+            }
+        }
+
+        // ---- combine triangle chunks of this node block (fixed order)
+        double mr = acc_r, mi = acc_i;
+        if (p.nchunks > 1) {
+            if (active) {
+                a.partial[2 * ((int64_t)chunk * n + node)] = acc_r;
+                a.partial[2 * ((int64_t)chunk * n + node) + 1] = acc_i;
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = (atomicAdd(&a.cnt[nb], 1) == p.nchunks - 1);
+            __syncthreads();
+            if (!s_last) continue;
+            __threadfence();
+            mr = 0.0;
+            mi = 0.0;
+            if (active)
+                for (int c = 0; c < p.nchunks; ++c) {
+                    mr += __ldcg(&a.partial[2 * ((int64_t)c * n + node)]);
+                    mi += __ldcg(&a.partial[2 * ((int64_t)c * n + node) + 1]);
+                }
+            if (threadIdx.x == 0) a.cnt[nb] = 0;  // ready for the next launch
+        }
+
+        if (MODE == MODE_FT) {
+            if (active) {
+                a.out[node] = mr;
+                a.out_im[node] = mi;
+            }
+            continue;
+        }
+
+        // ---- distance epilogue (a6, a7): subtract nu^, weight, reduce
+        double term = 0.0;
+        if (active) {
+            double dr = mr, di = mi;
+            if (a.nu) {
+                dr -= a.nu[2 * node];
+                di -= a.nu[2 * node + 1];
+            }
+            term = a.W[node] * (dr * dr + di * di);
+        }
+        const double bsum = block_sum(term, red);
+        if (threadIdx.x == 0) {
+            a.blockD[nb] = bsum;
+            __threadfence();
+            s_last = (atomicAdd(a.done, 1) == (int)(p.n_nb - 1));
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double v = 0.0;
+            for (int64_t i = threadIdx.x; i < p.n_nb; i += WD_NPB) v += __ldcg(&a.blockD[i]);
+            const double tot = block_sum(v, red);
+            if (threadIdx.x == 0) {
+                a.out[0] = tot;
+                *a.done = 0;
+            }
+        }
+    }
+}
+
+template <bool MIXED, int MODE>
+int resident_blocks(wd_ctx* ctx)
+{
+    static int cached[64] = {0};
+    int& c = cached[ctx->device & 63];
+    if (c == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel<MIXED, MODE>, WD_NPB, 0) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        c = per_sm * ctx->num_sms;
+    }
+    return c;
+}
+
+int resident_for(wd_ctx* ctx, int precision, int mode)
+{
+    if (precision == WD_MIXED)
+        return mode == MODE_FT ? resident_blocks<true, MODE_FT>(ctx) : resident_blocks<true, MODE_DIST>(ctx);
+    return mode == MODE_FT ? resident_blocks<false, MODE_FT>(ctx) : resident_blocks<false, MODE_DIST>(ctx);
+}
+
+}  // namespace
+
+size_t wd_tri_record_bytes(int precision)
+{
+    return precision == WD_MIXED ? sizeof(TriRecF) : sizeof(TriRecD);
+}
+
+wd_status wd_launch_stage(wd_ctx* ctx, int precision, const double* d_verts, int64_t nv,
+                          const int32_t* d_tris, int64_t nt, double sign, void* d_rec,
+                          int64_t rec_offset, cudaStream_t st)
+{
+    if (nt == 0) return WD_OK;
+    int64_t g = (nt + 255) / 256;
+    const int64_t cap = (int64_t)ctx->num_sms * 8;
+    if (g > cap) g = cap;
+    if (precision == WD_MIXED)
+        stage_kernel<true><<<(int)g, 256, 0, st>>>(d_verts, nv, d_tris, nt, sign,
+                                                     static_cast<TriRecF*>(d_rec) + rec_offset, ctx->d_flags);
+    else
+        stage_kernel<false><<<(int)g, 256, 0, st>>>(d_verts, nv, d_tris, nt, sign,
+                                                      static_cast<TriRecD*>(d_rec) + rec_offset, ctx->d_flags);
+    ctx->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+wd_status wd_plan_pair(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, int64_t n_tris,
+                       PairPlan* plan)
+{
+    PairPlan p;
+    p.n_nodes = n_nodes;
+    p.n_tris = n_tris;
+    p.n_nb = (n_nodes + WD_NPB - 1) / WD_NPB;
+    p.n_tiles = (n_tris + WD_TILE - 1) / WD_TILE;
+    const int64_t resident = resident_for(ctx, precision, mode);
+    // split the triangle range only when node blocks alone cannot fill the GPU
+    const int64_t target = 4 * resident;
+    int64_t nchunks = 1;
+    if (p.n_nb > 0 && p.n_nb < target && p.n_tiles > 1) {
+        nchunks = (target + p.n_nb - 1) / p.n_nb;
+        if (nchunks > p.n_tiles) nchunks = p.n_tiles;
+    }
+    int64_t tpc = p.n_tiles > 0 ? (p.n_tiles + nchunks - 1) / nchunks : 0;
+    if (tpc > 0) nchunks = (p.n_tiles + tpc - 1) / tpc;
+    if (nchunks < 1) nchunks = 1;
+    p.tiles_per_chunk = (int)tpc;
+    p.nchunks = (int)nchunks;
+    p.n_items = p.n_nb * p.nchunks;
+    p.grid = (int)(p.n_items < resident ? p.n_items : resident);
+    *plan = p;
+    return WD_OK;
+}
+
+wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
+                         const PairArgs& args, cudaStream_t st)
+{
+    if (plan.n_items == 0) return WD_OK;
+    if (precision == WD_MIXED) {
+        if (mode == MODE_FT) pair_kernel<true, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        else pair_kernel<true, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+    } else {
+        if (mode == MODE_FT) pair_kernel<false, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        else pair_kernel<false, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+    }
+    ctx->launches++;
+    WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
