@@ -191,6 +191,39 @@ wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule, const double* d
  * points). Used to report launch counts. */
 int64_t wd_launch_count(const wd_ctx* ctx);
 
+/* ------------------------------------------------------------ allocation-free variant */
+
+/* Fixed size of the library's static device scratch used below (64 MiB). */
+#define WD_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory while they run: applications whose own
+ * memory manager owns the device, latency-critical loops that may not touch
+ * cudaMalloc/cudaFree (which can synchronise the device), and plugins that
+ * only get buffers from their host. It computes the same D as wd_distance_dev
+ * with a sphere as reference, using the same kernels, but takes every input
+ * as a caller-owned device array and needs no context and no rule handle:
+ *   d_xi      frequency nodes, SoA (x[n], y[n], z[n]) float64
+ *   d_w_geom  s-free node weights, n float64 (as from wd_rule_copy_nodes)
+ *   d_verts, d_tris  the mesh, as for wd_distance_dev
+ *   radius, center   the reference sphere
+ *   d_dist2   one float64 output, written when the stream reaches the call
+ * It runs on the calling thread's current device. All intermediate storage
+ * lives in one static array of WD_NOALLOC_SCRATCH_BYTES that every device
+ * loading the library reserves until the process exits; a problem needing
+ * more is rejected with WD_EINVAL and a message giving the size. The call
+ * makes no device allocation. Its first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the one array, and counters in it are
+ * cleared at each call: calls whose work overlaps on the GPU (different
+ * streams, or other host threads) race and must be serialised by the caller.
+ * Triangle indices are not validated on the host: an out-of-range index or a
+ * non-finite vertex makes that triangle contribute zero. */
+wd_status wd_distance_dev_noalloc(const double* d_xi, const double* d_w_geom, int64_t n_nodes,
+                                  const double* d_verts, int64_t n_verts, const int32_t* d_tris,
+                                  int64_t n_tris, double s, double radius, const double center[3],
+                                  int precision, double* d_dist2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ _sig("wd_distance_grad", [_vp, _vp, ctypes.POINTER(wd_mesh), ctypes.POINTER(wd_m
 _sig("wd_distance_grad_dev", [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(wd_measure), ctypes.c_double,
                               ctypes.c_int, _vp, _vp, _vp])
 _sig("wd_launch_count", [_vp], _i64)
+_sig("wd_distance_dev_noalloc", [_vp, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, ctypes.c_double, _dp,
+                                 ctypes.c_int, _vp, _vp])
 
 
 class WDError(RuntimeError):
@@ -267,6 +269,16 @@ def wd_distance_grad_dev(ctx, rule, verts, tris, nu, s, precision, out, grad, st
 
 def wd_launch_count(ctx):
     return int(_lib.wd_launch_count(ctx))
+
+
+def wd_distance_dev_noalloc(xi_soa, w_geom, verts, tris, s, radius, center, precision, out, stream=None):
+    """Allocation-free distance (see include/wd.h): xi_soa is a (3, n) float64
+    CUDA tensor, w_geom (n,), verts (V, 3) float64, tris (T, 3) int32, out one
+    float64 element. Runs on the current CUDA device."""
+    c = np.ascontiguousarray(center, dtype=np.float64)
+    _check(_lib.wd_distance_dev_noalloc(_dev_ptr(xi_soa), _dev_ptr(w_geom), w_geom.shape[0], _dev_ptr(verts),
+                                        verts.shape[0], _dev_ptr(tris), tris.shape[0], float(s), float(radius),
+                                        c.ctypes.data_as(_dp), int(precision), _dev_ptr(out), _stream(stream)))
 
 
 class Context:
