@@ -106,8 +106,9 @@ __device__ constexpr double kInvFact2[23] = {
     1.0 / 51090942171709440000.0, 1.0 / 1124000727777607680000.0,
     1.0 / 25852016738884976640000.0, 1.0 / 620448401733239439360000.0};
 
-// sum_n (-i)^n h_n / (n+2)! with h_n = p h_{n-2} + q h_{n-3}
-template <typename Real, int NT>
+// sum_n (-i)^n h_n / (n+2)! with h_n = p h_{n-2} + q h_{n-3}, from n = N0
+// (N0 = 0: the full series; N0 = 3: the tail after the 1/2 and -p/24 terms)
+template <typename Real, int NT, int N0 = 0>
 __device__ __forceinline__ void taylor_sum(Real p, Real q, Real& sr, Real& si)
 {
     Real h[NT + 1];
@@ -120,7 +121,7 @@ __device__ __forceinline__ void taylor_sum(Real p, Real q, Real& sr, Real& si)
     sr = Real(0);
     si = Real(0);
 #pragma unroll
-    for (int n = NT; n >= 0; --n) {
+    for (int n = NT; n >= N0; --n) {
         // (-i)^n: 1, -i, -1, i
         const Real c = Real(kInvFact2[n]);
         switch (n & 3) {
@@ -196,7 +197,27 @@ struct NodeF {
     float x, y, z;     // xi (radians), float32
     float hx, hy, hz;  // xi / 2 pi, high float32 part
     float lx, ly, lz;  // xi / 2 pi - high part
+    float dith;        // per-node phase origin shift in turns, [0, 1)
 };
+
+// Per-node phase dither. The float32 rounding of each pair's terms is a
+// deterministic function of its phases; at low frequency neighbouring nodes
+// see nearly equal phases, round alike, and the per-node errors add up
+// coherently in the weighted sum against mu^ - nu^, which is small there.
+// Shifting every phase of node k by a pseudo-random turn offset d_k and
+// rotating the node's sum back by exp(-2 pi i d_k) in float64 leaves the
+// result unchanged (translation theorem) while making the rounding errors of
+// different nodes independent, so they average out in the quadrature sum.
+__device__ __forceinline__ float node_dither(int64_t node)
+{
+    uint32_t h = (uint32_t)node * 0x9E3779B9u + 0x7F4A7C15u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (float)(h >> 8) * 5.9604644775390625e-8f;  // 24 bits, exact in float32
+}
 
 // sin(x)/x: reduction by the nearest multiple of pi (two-constant split) and
 // the Taylor polynomial of sin(r)/r on |r| <= pi/2 (remainder < 5e-10).
@@ -221,40 +242,61 @@ __device__ __forceinline__ float sinc32(float x)
     return P * qf;
 }
 
-// exp(-i 2 pi tau) for tau in turns, without rounding 2 pi into the argument:
-// reduction to the nearest quarter turn (exact), x = 2 pi u carried as a float
-// pair, Taylor polynomials of sin and cos on |x| <= pi/4 (remainders below
-// 2e-9), and a quarter-turn rotation by selects.
-__device__ __forceinline__ void expm_turns(float tau, float& er, float& ei)
+// exp(-i 2 pi tau) for a phase in turns given as the unevaluated float pair
+// tau + tlo, without rounding 2 pi into the argument. tau = j/64 + u with j
+// the nearest multiple (found with a magic-number add, so no float-to-int
+// conversion) and |u| <= 1/128 exactly; exp(-2 pi i j/64) comes from a table
+// of float pairs (hi + lo, from float64 sincospi), exp(-i x), x = 2 pi u, from
+// short Taylor polynomials (|x| <= pi/64: remainders below 1e-13), and the two
+// are combined in pair arithmetic. Unlike a float32 polynomial on a quarter
+// turn, whose rounded coefficients bias its mean amplitude by about 1e-9,
+// this has a mean relative bias near 1e-11, which matters because the phases
+// of a node's triangles are uniformly spread and any mean bias scales mu^.
+constexpr int kTab = 64;
+struct __align__(16) TabEntry {
+    float ch, cl, sh, sl;  // cos and sin of 2 pi j / 64 as float pairs
+};
+
+__device__ __forceinline__ void fill_exp_table(TabEntry* tab)
 {
-    const float k = rintf(4.0f * tau);
-    const float u = fmaf(-0.25f, k, tau);  // exact, |u| <= 1/8
-    const float xh = u * 6.28318548202514648f;
-    float xl = fmaf(u, 6.28318548202514648f, -xh);
-    xl = fmaf(u, -1.74845553e-7f, xl);     // 2 pi - float(2 pi)
-    const float x2 = xh * xh;
-    float ps = 1.0f / 362880.0f;
-    ps = fmaf(ps, x2, -1.0f / 5040.0f);
-    ps = fmaf(ps, x2, 1.0f / 120.0f);
-    ps = fmaf(ps, x2, -1.0f / 6.0f);
-    const float sn = xh + fmaf(xh * x2, ps, xl);
-    float pc = -1.0f / 3628800.0f;
-    pc = fmaf(pc, x2, 1.0f / 40320.0f);
-    pc = fmaf(pc, x2, -1.0f / 720.0f);
-    pc = fmaf(pc, x2, 1.0f / 24.0f);
-    const float cs = 1.0f + fmaf(x2 * x2, pc, fmaf(-0.5f, x2, -xh * xl));
-    // rotate by k quarter turns; k4 = k mod 4 in {-2, -1, 0, 1, 2}
-    const float k4 = fmaf(-4.0f, rintf(0.25f * k), k);
-    const bool sw = fabsf(k4) == 1.0f;
-    const float a = sw ? cs : sn;
-    const float b = sw ? sn : cs;
-    const float sin_t = (k4 < 0.0f || k4 > 1.5f) ? -a : a;
-    const float cos_t = (k4 > 0.5f || k4 < -1.5f) ? -b : b;
-    er = cos_t;  // exp(-i theta) = cos theta - i sin theta
-    ei = -sin_t;
+    for (int j = threadIdx.x; j < kTab; j += blockDim.x) {
+        double sd, cd;
+        sincospi(2.0 * j / kTab, &sd, &cd);
+        TabEntry e;
+        e.ch = (float)cd;
+        e.cl = (float)(cd - (double)e.ch);
+        e.sh = (float)sd;
+        e.sl = (float)(sd - (double)e.sh);
+        tab[j] = e;
+    }
 }
 
-__device__ __forceinline__ void pair_mixed(const NodeF& q, const TriRecF& t, float& fr, float& fi)
+__device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tab, float tau, float tlo,
+                                           float& er, float& ei)
+{
+    const float magic = 12582912.0f;  // 1.5 * 2^23: rounds to an integer in the low bits
+    const float km = fmaf(tau, (float)kTab, magic);
+    const int idx = __float_as_int(km) & (kTab - 1);
+    const float k = km - magic;                   // exact
+    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/128
+    const float xh = u * 6.28318548202514648f;
+    float xl = fmaf(u, 6.28318548202514648f, -xh);
+    xl = fmaf(u, -1.74845553e-7f, xl);            // 2 pi - float(2 pi)
+    xl = fmaf(tlo, 6.28318548202514648f, xl);
+    const float x2 = xh * xh;
+    // cos x - 1 and sin x - xh
+    const float dc = fmaf(fmaf(x2, -1.0f / 720.0f, 1.0f / 24.0f), x2 * x2, fmaf(-0.5f, x2, -xh * xl));
+    const float ds = fmaf(xh * x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), xl);
+    const TabEntry t = tab[idx];
+    // cos(theta) = Tc (1 + dc) - Ts sin x, sin(theta) = Ts (1 + dc) + Tc sin x
+    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, xh, t.cl + fmaf(-t.sh, ds, -t.sl * xh)));
+    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, xh, t.sl + fmaf(t.ch, ds, t.cl * xh)));
+    er = c;   // exp(-i theta) = cos theta - i sin theta
+    ei = -s;
+}
+
+__device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, const NodeF& q, const TriRecF& t,
+                                           float& fr, float& fi)
 {
     // centroid phase in turns: exact high products reduced mod 1, plus the low terms
     const float p0 = q.hx * t.mh[0], p1 = q.hy * t.mh[1], p2 = q.hz * t.mh[2];
@@ -272,7 +314,11 @@ __device__ __forceinline__ void pair_mixed(const NodeF& q, const TriRecF& t, flo
     lo = fmaf(q.lx, t.mh[0], lo);
     lo = fmaf(q.ly, t.mh[1], lo);
     lo = fmaf(q.lz, t.mh[2], lo);
-    const float tau = f + lo;  // turns
+    // phase in turns as the pair (tau, tlo), shifted by the node's dither:
+    // tau = f - dith exactly rounded, its error folded into tlo (two-sum)
+    const float tau = f - q.dith;
+    const float bb = tau - f;
+    const float tlo = ((f - (tau - bb)) + (-q.dith - bb)) + lo;
     const float g1 = fmaf(q.x, t.e1[0], fmaf(q.y, t.e1[1], q.z * t.e1[2]));
     const float g2 = fmaf(q.x, t.e2[0], fmaf(q.y, t.e2[1], q.z * t.e2[2]));
     const float g3 = g2 - g1;
@@ -285,12 +331,30 @@ __device__ __forceinline__ void pair_mixed(const NodeF& q, const TriRecF& t, flo
     if (gmax < kDelta32) {
         const float p = (g1 * g1 - g1 * g2 + g2 * g2) * (1.0f / 3.0f);
         const float qq = ya * yb * yc;
+        // The series value depends only on the gaps, so its rounding repeats at
+        // neighbouring nodes; the exact leading 1/2 is therefore kept out of it
+        // and applied with the (dithered) phase factor, and only the small tail
+        // sr + i si = Psi - 1/2 = O(p) is rounded independently of the phase.
+        // The -p/24 term is formed as -A/72 with A = g1^2 - g1 g2 + g2^2 and
+        // 1/72 as a float pair: a rounded 1/3 or 1/24 would bias it the same
+        // way for every triangle.
+        const float A = fmaf(g1, g1 - g2, g2 * g2);
         float sr, si;
-        taylor_sum<float, kTerms32>(p, qq, sr, si);
+        taylor_sum<float, kTerms32, 3>(p, qq, sr, si);
+        sr = fmaf(A, -1.388888899e-02f, fmaf(A, 1.034802868e-10f, sr));  // -A (1/72 hi + lo)
         float c, s;
-        expm_turns(tau, c, s);  // (c, s) = exp(-i t_m)
-        gr = c * sr - s * si;
-        gi = c * si + s * sr;
+        expm_turns(tab, tau, tlo, c, s);  // (c, s) = exp(-i (t_m - 2 pi dith))
+        // G = (c + i s)(1/2 + sr + i si). The tail must not be added to the
+        // exactly representable c/2 on its own: below half an ulp it would be
+        // rounded away every time, and it has one sign (-p/24), so the loss
+        // would be a bias. It is added inside the final rounding with gamma,
+        // where gamma c/2 is a full-width product off the float grid.
+        const float hc = 0.5f * c, hs = 0.5f * s;  // exact
+        const float tr = fmaf(c, sr, -s * si);
+        const float ti = fmaf(c, si, s * sr);
+        fr = fmaf(t.gam, hc, fmaf(t.gam, tr, t.gam_lo * (hc + tr)));
+        fi = fmaf(t.gam, hs, fmaf(t.gam, ti, t.gam_lo * (hs + ti)));
+        return;
     } else {
         const bool caseA = (a2 >= a1) && (a2 >= a3);
         const bool caseB = !caseA && (a1 >= a3);
@@ -302,8 +366,8 @@ __device__ __forceinline__ void pair_mixed(const NodeF& q, const TriRecF& t, flo
         const float hQ = caseB ? 0.5f * g2 : 0.5f * g1;
         const float D = caseA ? g2 : (caseB ? g1 : g3);
         float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
-        expm_turns(tau + offP, cP, sP);
-        expm_turns(tau + offQ, cQ, sQ);
+        expm_turns(tab, tau + offP, tlo, cP, sP);
+        expm_turns(tab, tau + offQ, tlo, cQ, sQ);
         const float scP = sinc32(hP), scQ = sinc32(hQ);
         // S_P - S_Q, G = i (S_P - S_Q) / D
         const float dr = cP * scP - cQ * scQ;
@@ -358,6 +422,8 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
     __shared__ __align__(16) Rec tile[WD_TILE];
     __shared__ double red[WD_NPB / 32];
     __shared__ int s_last;
+    __shared__ TabEntry etab[kTab];
+    if (MIXED) fill_exp_table(etab);  // visible after the first tile barrier
 
     const int64_t n = a.n;
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
@@ -384,6 +450,7 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
             qf.lx = (float)(X - (double)qf.hx);
             qf.ly = (float)(Y - (double)qf.hy);
             qf.lz = (float)(Z - (double)qf.hz);
+            qf.dith = node_dither(node);
         }
         const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
         int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
@@ -403,7 +470,7 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
 #pragma unroll 2
                 for (int j = 0; j < cnt; ++j) {
                     float fr, fi;
-                    pair_mixed(qf, reinterpret_cast<const TriRecF*>(tile)[j], fr, fi);
+                    pair_mixed(etab, qf, reinterpret_cast<const TriRecF*>(tile)[j], fr, fi);
                     kr.add(fr);
                     ki.add(fi);
                 }
@@ -440,6 +507,15 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
                     mi += __ldcg(&a.partial[2 * ((int64_t)c * n + node) + 1]);
                 }
             if (threadIdx.x == 0) a.cnt[nb] = 0;  // ready for the next launch
+        }
+
+        if (MIXED) {
+            // undo the phase dither: mu^ = S exp(-2 pi i dith), in float64
+            double sd, cd;
+            sincospi(2.0 * (double)qf.dith, &sd, &cd);
+            const double r_ = mr * cd + mi * sd;
+            mi = mi * cd - mr * sd;
+            mr = r_;
         }
 
         if (MODE == MODE_FT) {

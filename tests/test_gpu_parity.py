@@ -214,3 +214,22 @@ def test_device_path_matches_host_path(ctx, prec):
     wd.wd_sync(ctx.handle)
     host_ft = ctx.mesh_ft(rule, v, t, prec)
     assert np.array_equal(re.cpu().numpy(), host_ft.real) and np.array_equal(im.cpu().numpy(), host_ft.imag)
+
+
+@pytest.mark.parametrize("n, shells", [(32, None), (64, 32)])
+@pytest.mark.parametrize("s", [1.0, 2.0])
+def test_mixed_matches_fp64_on_the_refinement_sweep(ctx, n, shells, s):
+    """Mixed vs float64 on the sweep rule (R = 128, 192 x 96 x 192, Hermitian):
+    the full rule for n = 32, and for n = 64 the 32 lowest radial shells, where
+    D for s = 2 is small next to the mesh transform and any coherent float32
+    error would show first. Bar: 1e-6 relative."""
+    R = synth.SWEEP_RULE
+    rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+    if shells is not None:
+        xi, w = wd.wd_rule_copy_nodes(rule)
+        per = len(xi) // R.n_r
+        rule = ctx.rule_from_nodes(xi[: shells * per], w[: shells * per])
+    v, t = synth.icosphere(n)
+    d64 = ctx.distance(rule, v, t, None, s, FP64)
+    dmx = ctx.distance(rule, v, t, None, s, MIXED)
+    assert abs(dmx - d64) < 1e-6 * d64, (dmx, d64, (dmx - d64) / d64)
