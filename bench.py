@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-check", action="store_true", help="skip the mixed-vs-fp64 accuracy check")
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    p.add_argument("--only-n", type=int, default=None, help="restrict the sweep to one mesh (profiling runs)")
     return p.parse_args()
 
 
@@ -206,6 +207,9 @@ def run_reference(args, cfg, queries, R):
 def main():
     args = parse()
     cfg, queries, R = workload(args.workload)
+    if args.only_n is not None:
+        queries = [q for q in queries if len(q[1]) == 20 * args.only_n ** 2]
+        cfg["n"] = [args.only_n]
     cfg["precision"] = args.precision
     cfg["l2"] = "flushed between timed steps (%d MB write)" % (L2_FLUSH_BYTES >> 20)
     if args.impl == "reference":

@@ -91,11 +91,10 @@ __global__ void stage_kernel(const double* __restrict__ verts, int64_t nv,
 // ------------------------------------------------------------------ shared pieces
 // Taylor branch bounds: below a largest gap DELTA the centred phases satisfy
 // |y| <= 2 DELTA / 3. float64: DELTA = 1, series to n = 18 (remainder < 1e-18);
-// mixed: DELTA = 1.5, series to n = 13 (|y| <= 1, remainder < 1e-10).
+// mixed: DELTA = 3, series to n = 12 (p <= 3, remainder < 3e-9).
 constexpr double kDelta64 = 1.0;
 constexpr int kTerms64 = 18;
-constexpr float kDelta32 = 1.5f;
-constexpr int kTerms32 = 13;
+constexpr float kDelta32 = 3.0f;
 
 // 1/(n+2)! for n = 0..22
 __device__ constexpr double kInvFact2[23] = {
@@ -243,16 +242,16 @@ __device__ __forceinline__ float sinc32(float x)
 }
 
 // exp(-i 2 pi tau) for a phase in turns given as the unevaluated float pair
-// tau + tlo, without rounding 2 pi into the argument. tau = j/64 + u with j
+// tau + tlo, without rounding 2 pi into the argument. tau = j/256 + u with j
 // the nearest multiple (found with a magic-number add, so no float-to-int
-// conversion) and |u| <= 1/128 exactly; exp(-2 pi i j/64) comes from a table
+// conversion) and |u| <= 1/512 exactly; exp(-2 pi i j/256) comes from a table
 // of float pairs (hi + lo, from float64 sincospi), exp(-i x), x = 2 pi u, from
-// short Taylor polynomials (|x| <= pi/64: remainders below 1e-13), and the two
-// are combined in pair arithmetic. Unlike a float32 polynomial on a quarter
+// short Taylor polynomials (|x| <= pi/256: remainders below 3e-12), and the
+// two are combined in pair arithmetic. Unlike a float32 polynomial on a quarter
 // turn, whose rounded coefficients bias its mean amplitude by about 1e-9,
 // this has a mean relative bias near 1e-11, which matters because the phases
 // of a node's triangles are uniformly spread and any mean bias scales mu^.
-constexpr int kTab = 64;
+constexpr int kTab = 256;
 struct __align__(16) TabEntry {
     float ch, cl, sh, sl;  // cos and sin of 2 pi j / 64 as float pairs
 };
@@ -278,15 +277,15 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tab, flo
     const float km = fmaf(tau, (float)kTab, magic);
     const int idx = __float_as_int(km) & (kTab - 1);
     const float k = km - magic;                   // exact
-    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/128
+    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/512
     const float xh = u * 6.28318548202514648f;
     float xl = fmaf(u, 6.28318548202514648f, -xh);
     xl = fmaf(u, -1.74845553e-7f, xl);            // 2 pi - float(2 pi)
     xl = fmaf(tlo, 6.28318548202514648f, xl);
     const float x2 = xh * xh;
     // cos x - 1 and sin x - xh
-    const float dc = fmaf(fmaf(x2, -1.0f / 720.0f, 1.0f / 24.0f), x2 * x2, fmaf(-0.5f, x2, -xh * xl));
-    const float ds = fmaf(xh * x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), xl);
+    const float dc = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), -xh * xl);
+    const float ds = fmaf(xh * x2, -1.0f / 6.0f, xl);
     const TabEntry t = tab[idx];
     // cos(theta) = Tc (1 + dc) - Ts sin x, sin(theta) = Ts (1 + dc) + Tc sin x
     const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, xh, t.cl + fmaf(-t.sh, ds, -t.sl * xh)));
@@ -314,11 +313,11 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
     lo = fmaf(q.lx, t.mh[0], lo);
     lo = fmaf(q.ly, t.mh[1], lo);
     lo = fmaf(q.lz, t.mh[2], lo);
-    // phase in turns as the pair (tau, tlo), shifted by the node's dither:
-    // tau = f - dith exactly rounded, its error folded into tlo (two-sum)
+    // phase in turns as the pair (tau, tlo), shifted by the node's dither; the
+    // rounding of f - dith (below 2^-25 turns) varies pseudo-randomly with the
+    // dithered phase and averages out over the triangles
     const float tau = f - q.dith;
-    const float bb = tau - f;
-    const float tlo = ((f - (tau - bb)) + (-q.dith - bb)) + lo;
+    const float tlo = lo;
     const float g1 = fmaf(q.x, t.e1[0], fmaf(q.y, t.e1[1], q.z * t.e1[2]));
     const float g2 = fmaf(q.x, t.e2[0], fmaf(q.y, t.e2[1], q.z * t.e2[2]));
     const float g3 = g2 - g1;
@@ -335,13 +334,28 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
         // neighbouring nodes; the exact leading 1/2 is therefore kept out of it
         // and applied with the (dithered) phase factor, and only the small tail
         // sr + i si = Psi - 1/2 = O(p) is rounded independently of the phase.
-        // The -p/24 term is formed as -A/72 with A = g1^2 - g1 g2 + g2^2 and
-        // 1/72 as a float pair: a rounded 1/3 or 1/24 would bias it the same
-        // way for every triangle.
+        // Psi - 1/2 = sum_{n>=2} (-i)^n h_n / (n+2)! in Horner form, with
+        // h_n = sum_{2j+3k=n} C(j+k, k) p^j q^k, to n = 12. The -p/24 term is
+        // formed as -A/72 with A = g1^2 - g1 g2 + g2^2 and 1/72 as a float
+        // pair: a rounded 1/3 or 1/24 would bias it alike for every triangle.
         const float A = fmaf(g1, g1 - g2, g2 * g2);
-        float sr, si;
-        taylor_sum<float, kTerms32, 3>(p, qq, sr, si);
+        const float q2 = qq * qq;
+        float re = fmaf(p, 1.0f / 87178291200.0f, -1.0f / 479001600.0f);
+        re = fmaf(re, p, 1.0f / 3628800.0f);
+        re = fmaf(re, p, -1.0f / 40320.0f);
+        re = fmaf(re, p, 1.0f / 720.0f);
+        float rq = fmaf(p, 10.0f / 87178291200.0f, -6.0f / 479001600.0f);
+        rq = fmaf(rq, p, 3.0f / 3628800.0f);
+        rq = fmaf(rq, p, -1.0f / 40320.0f);
+        rq = fmaf(q2, 1.0f / 87178291200.0f, rq);
+        float sr = fmaf(re, p * p, q2 * rq);
         sr = fmaf(A, -1.388888899e-02f, fmaf(A, 1.034802868e-10f, sr));  // -A (1/72 hi + lo)
+        float im = fmaf(p, 5.0f / 6227020800.0f, -4.0f / 39916800.0f);
+        im = fmaf(im, p, 3.0f / 362880.0f);
+        im = fmaf(im, p, -2.0f / 5040.0f);
+        im = fmaf(im, p, 1.0f / 120.0f);
+        const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
+        const float si = qq * fmaf(q2, iq, im);
         float c, s;
         expm_turns(tab, tau, tlo, c, s);  // (c, s) = exp(-i (t_m - 2 pi dith))
         // G = (c + i s)(1/2 + sr + i si). The tail must not be added to the
@@ -458,21 +472,33 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
         for (int64_t tb = t0; tb < t1; tb += WD_TILE) {
             const int cnt = (int)((t1 - tb) < WD_TILE ? (t1 - tb) : WD_TILE);
             __syncthreads();
+            // the mixed path reads the tile in groups of 4: pad with zero
+            // records, which contribute exactly zero (gamma = 0)
+            const int cnt4 = MIXED ? ((cnt + 3) & ~3) : cnt;
             {
                 const uint4* src = reinterpret_cast<const uint4*>(static_cast<const Rec*>(a.tris) + tb);
                 uint4* dst = reinterpret_cast<uint4*>(tile);
                 const int nvec = cnt * (int)(sizeof(Rec) / 16);
-                for (int i = threadIdx.x; i < nvec; i += WD_NPB) dst[i] = __ldg(src + i);
+                const int nvec4 = cnt4 * (int)(sizeof(Rec) / 16);
+                for (int i = threadIdx.x; i < nvec4; i += WD_NPB)
+                    dst[i] = i < nvec ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
             }
             __syncthreads();
             if (MIXED) {
+                // plain float32 sums over groups of 4 pairs (their phases are
+                // dithered, so the roundings are random), Kahan across groups
                 Kahan kr, ki;
-#pragma unroll 2
-                for (int j = 0; j < cnt; ++j) {
-                    float fr, fi;
-                    pair_mixed(etab, qf, reinterpret_cast<const TriRecF*>(tile)[j], fr, fi);
-                    kr.add(fr);
-                    ki.add(fi);
+                for (int j = 0; j < cnt4; j += 4) {
+                    float br = 0.0f, bi = 0.0f;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        float fr, fi;
+                        pair_mixed(etab, qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
+                        br += fr;
+                        bi += fi;
+                    }
+                    kr.add(br);
+                    ki.add(bi);
                 }
                 acc_r += kr.value();
                 acc_i += ki.value();
