@@ -39,6 +39,10 @@ UNIT = "Gpair/s"
 N_FP32_PER_PAIR = 60
 N_MUFU_PER_PAIR = 6
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
+# DRAM bytes (read + write) of one mixed pair-kernel launch on the n = 64 sweep
+# query, from ncu (profiles/pair_kernel_mixed_sweep_n64.md); None once the
+# kernel changes after that capture.
+PAIR_KERNEL_TRAFFIC_N64 = 94.0e6
 
 
 def parse():
@@ -338,7 +342,10 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = pair_roofline_peak(sm_count, peaks.get("sm_max_mhz", 2032.0))
     roof = {"bound": "alu", "achieved": pair_rate / 1e9, "peak": peak / 1e9, "unit": UNIT,
-            "frac": pair_rate / peak, "traffic": None,
+            "frac": pair_rate / peak,
+            "traffic": PAIR_KERNEL_TRAFFIC_N64 if prec == wd.WD_MIXED else None,
+            "traffic_note": "dram read+write bytes of the n=64 launch (ncu); algorithmic bytes per launch "
+                            "are the rule (32 B/node) and the mesh records (64 B/triangle), 62 MB",
             "kernel": "pair_kernel (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
             "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
                           % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
