@@ -396,21 +396,138 @@ extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_me
     return finish_host(ctx, strm);
 }
 
-extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule, const double*, int64_t,
-                                          const int32_t*, int64_t, const wd_measure*, double, int,
-                                          double*, double*, void*)
+// Gradient core on device pointers: forward pass in `precision` writing D and
+// the residual 2 W (mu^ - nu^), then the float64 adjoint over mu's triangles.
+static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const double* d_verts, int64_t nv,
+                           const int32_t* d_tris, int64_t nt, const wd_measure* nu, double s, double* d_dist2,
+                           double* d_grad, size_t base, cudaStream_t st)
 {
-    wd_status st = check_common(ctx, rule, WD_FP64);
-    if (st != WD_OK) return st;
-    wd_set_error("wd_distance_grad_dev: not available in this build");
-    return WD_EINVAL;
+    const int64_t nt2 = nu->kind == WD_NU_MESH ? nu->mesh->n_tris : 0;
+    const int64_t n = rule->n_eval;
+    CoreLayout L = core_layout(ctx, precision, MODE_RESID, n, nt + nt2, base);
+    AdjPlan ap;
+    wd_plan_adjoint(ctx, WD_FP64, n, nt, &ap);
+    size_t off = L.end;
+    const size_t o_res = off;
+    off += align_up(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    const size_t o_rec64 = off;
+    off += align_up(sizeof(TriRecD) * (size_t)(nt > 0 ? nt : 1));
+    const size_t o_adj = off;
+    off += align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) * (size_t)(nt > 0 ? nt : 1));
+    wd_status st_ = wd_ws_reserve(ctx, off);
+    if (st_ != WD_OK) return st_;
+    if ((st_ = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st_;
+    double* resid = reinterpret_cast<double*>(ctx->ws + o_res);
+    if (n > 0) WD_CUDA(cudaMemsetAsync(resid, 0, sizeof(double) * 2 * n, st));
+    if (nv > 0) WD_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(double) * 3 * nv, st));
+    // forward (same staging as the distance), with the residual written per node
+    void* rec = ctx->ws + L.rec;
+    if ((st_ = wd_launch_stage(ctx, precision, d_verts, nv, d_tris, nt, 1.0, rec, 0, st)) != WD_OK) return st_;
+    PairArgs a;
+    a.xi = rule->d_xi;
+    a.n = n;
+    a.tris = rec;
+    a.T = L.plan.n_tris;
+    if (nu->kind == WD_NU_MESH) {
+        if ((st_ = wd_launch_stage(ctx, precision, nu->mesh->verts, nu->mesh->n_verts, nu->mesh->tris,
+                                   nu->mesh->n_tris, -1.0, rec, nt, st)) != WD_OK)
+            return st_;
+    } else if ((st_ = wd_rule_sphere(ctx, rule, nu->radius, nu->center, &a.nu, st)) != WD_OK) {
+        return st_;
+    }
+    if ((st_ = wd_rule_weights(ctx, rule, s, &a.W, st)) != WD_OK) return st_;
+    a.partial = reinterpret_cast<double*>(ctx->ws + L.partial);
+    a.cnt = ctx->d_counters;
+    a.blockD = reinterpret_cast<double*>(ctx->ws + L.blockD);
+    a.done = ctx->d_flags + 1;
+    a.out = d_dist2;
+    a.resid = resid;
+    if (L.plan.n_items == 0) {
+        WD_CUDA(cudaMemsetAsync(d_dist2, 0, sizeof(double), st));
+        return WD_OK;
+    }
+    if ((st_ = wd_launch_pair(ctx, precision, MODE_RESID, L.plan, a, st)) != WD_OK) return st_;
+    // adjoint over mu's triangles, staged in float64
+    void* rec64 = ctx->ws + o_rec64;
+    if ((st_ = wd_launch_stage(ctx, WD_FP64, d_verts, nv, d_tris, nt, 1.0, rec64, 0, st)) != WD_OK) return st_;
+    return wd_launch_adjoint(ctx, WD_FP64, ap, rule->d_xi, n, resid, rec64, nt,
+                             reinterpret_cast<double*>(ctx->ws + o_adj), d_tris, nv, d_grad, st);
 }
 
-extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule, const wd_mesh*, const wd_measure*,
-                                      double, int, double*, double*)
+extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
+                                          int64_t nv, const int32_t* d_tris, int64_t nt, const wd_measure* nu,
+                                          double s, int precision, double* d_dist2, double* d_grad, void* stream)
 {
-    wd_status st = check_common(ctx, rule, WD_FP64);
+    wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
-    wd_set_error("wd_distance_grad: not available in this build");
-    return WD_EINVAL;
+    if ((st = check_nu(nu)) != WD_OK) return st;
+    WD_CHECK(std::isfinite(s) && s > 0.0, WD_EINVAL, "s must be finite and > 0");
+    WD_CHECK(nv >= 0 && nt >= 0, WD_EINVAL, "negative mesh size");
+    WD_CHECK((nt == 0 || (d_verts && d_tris)) && d_dist2 && (nv == 0 || d_grad), WD_EINVAL,
+             "null device pointer");
+    const int64_t nt2 = nu->kind == WD_NU_MESH ? nu->mesh->n_tris : 0;
+    WD_CHECK(nt + nt2 <= ((int64_t)1 << 31), WD_EINVAL, "too many triangles");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    return grad_core(ctx, const_cast<wd_rule*>(rule_c), precision, d_verts, nv, d_tris, nt, nu, s, d_dist2, d_grad,
+                     0, (cudaStream_t)stream);
+}
+
+extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mu, const wd_measure* nu,
+                                      double s, int precision, double* dist2, double* grad_verts)
+{
+    wd_status st = check_common(ctx, rule_c, precision);
+    if (st != WD_OK) return st;
+    if ((st = check_nu(nu)) != WD_OK) return st;
+    WD_CHECK(std::isfinite(s) && s > 0.0, WD_EINVAL, "s must be finite and > 0");
+    WD_CHECK(dist2 && (mu == nullptr || mu->n_verts == 0 || grad_verts), WD_EINVAL, "null output");
+    std::string why;
+    WD_CHECK(host_mesh_ok(mu, &why), WD_EINVAL, why);
+    if (nu->kind == WD_NU_MESH) WD_CHECK(host_mesh_ok(nu->mesh, &why), WD_EINVAL, "reference mesh: " + why);
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    wd_rule* rule = const_cast<wd_rule*>(rule_c);
+    const wd_mesh* m2 = nu->kind == WD_NU_MESH ? nu->mesh : nullptr;
+    // upload area: mu, nu mesh, gradient; the core's scratch follows
+    size_t ov = 0, ot = align_up(sizeof(double) * 3 * mu->n_verts);
+    size_t ov2 = ot + align_up(sizeof(int32_t) * 3 * mu->n_tris);
+    size_t ot2 = ov2 + (m2 ? align_up(sizeof(double) * 3 * m2->n_verts) : 0);
+    size_t og = ot2 + (m2 ? align_up(sizeof(int32_t) * 3 * m2->n_tris) : 0);
+    size_t base = og + align_up(sizeof(double) * 3 * (size_t)(mu->n_verts > 0 ? mu->n_verts : 1));
+    // reserve the upload area first; grad_core grows the scratch beyond `base`
+    // before it touches any of it, and the uploads are issued after that
+    if ((st = wd_ws_reserve(ctx, base)) != WD_OK) return st;
+    cudaStream_t strm = 0;
+    // grad_core may reallocate the scratch, so size it first with a dry layout
+    {
+        const int64_t nt2 = m2 ? m2->n_tris : 0;
+        CoreLayout L = core_layout(ctx, precision, MODE_RESID, rule->n_eval, mu->n_tris + nt2, base);
+        AdjPlan ap;
+        wd_plan_adjoint(ctx, WD_FP64, rule->n_eval, mu->n_tris, &ap);
+        size_t need = L.end + align_up(sizeof(double) * 2 * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1)) +
+                      align_up(sizeof(TriRecD) * (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
+                      align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) *
+                               (size_t)(mu->n_tris > 0 ? mu->n_tris : 1));
+        if ((st = wd_ws_reserve(ctx, need)) != WD_OK) return st;
+    }
+    if ((st = upload_mesh(ctx, mu, ov, ot, strm)) != WD_OK) return st;
+    wd_mesh dm2{};
+    wd_measure dnu = *nu;
+    if (m2) {
+        if ((st = upload_mesh(ctx, m2, ov2, ot2, strm)) != WD_OK) return st;
+        dm2.verts = reinterpret_cast<const double*>(ctx->ws + ov2);
+        dm2.n_verts = m2->n_verts;
+        dm2.tris = reinterpret_cast<const int32_t*>(ctx->ws + ot2);
+        dm2.n_tris = m2->n_tris;
+        dnu.mesh = &dm2;
+    }
+    double* d_grad = reinterpret_cast<double*>(ctx->ws + og);
+    st = grad_core(ctx, rule, precision, reinterpret_cast<const double*>(ctx->ws + ov), mu->n_verts,
+                   reinterpret_cast<const int32_t*>(ctx->ws + ot), mu->n_tris, &dnu, s, ctx->d_scalar, d_grad, base,
+                   strm);
+    if (st != WD_OK) return st;
+    WD_CUDA(cudaMemcpyAsync(dist2, ctx->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, strm));
+    if (mu->n_verts > 0)
+        WD_CUDA(cudaMemcpyAsync(grad_verts, d_grad, sizeof(double) * 3 * mu->n_verts, cudaMemcpyDeviceToHost, strm));
+    return finish_host(ctx, strm);
 }

@@ -94,7 +94,7 @@ wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double
                          const double** d_nu, cudaStream_t st);
 
 // ------------------------------------------------------------------ kernels
-enum PairMode { MODE_DIST = 0, MODE_FT = 1 };
+enum PairMode { MODE_DIST = 0, MODE_FT = 1, MODE_RESID = 2 };
 
 struct PairPlan {
     int64_t n_nodes = 0;
@@ -120,6 +120,7 @@ struct PairArgs {
     int* done = nullptr;          // final-block counter
     double* out = nullptr;        // MODE_DIST: D; MODE_FT: re[n]
     double* out_im = nullptr;     // MODE_FT: im[n]
+    double* resid = nullptr;      // MODE_RESID: 2 W_k (mu^ - nu^)(xi_k), (re, im) interleaved
 };
 
 constexpr int WD_NPB = 256;   // nodes per block: one node per thread
@@ -138,5 +139,19 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
 wd_status wd_launch_sphere(wd_ctx* ctx, const double* d_xi, int64_t n, double radius,
                            const double* center, double* d_re, double* d_im, double* d_inter,
                            cudaStream_t st);
+// adjoint (wd_adjoint.cu): gradient of D with respect to the vertices of mu
+struct AdjPlan {
+    int64_t n_tb = 0;        // triangle blocks
+    int64_t n_node_tiles = 0;
+    int tiles_per_chunk = 0;
+    int nchunks = 0;
+    int64_t n_items = 0;
+    int grid = 0;
+};
+wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n_tris, AdjPlan* plan);
+wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
+                            const double* d_resid, const void* d_rec, int64_t nt, double* d_partial,
+                            const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st);
+
 wd_status wd_launch_weights(wd_ctx* ctx, const double* d_xi, const double* d_wg, int64_t n,
                             double s, double* d_w, cudaStream_t st);

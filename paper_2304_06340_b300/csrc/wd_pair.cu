@@ -561,6 +561,10 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
                 di -= a.nu[2 * node + 1];
             }
             term = a.W[node] * (dr * dr + di * di);
+            if (MODE == MODE_RESID) {
+                a.resid[2 * node] = 2.0 * a.W[node] * dr;
+                a.resid[2 * node + 1] = 2.0 * a.W[node] * di;
+            }
         }
         const double bsum = block_sum(term, red);
         if (threadIdx.x == 0) {
@@ -602,9 +606,14 @@ int resident_blocks(wd_ctx* ctx)
 
 int resident_for(wd_ctx* ctx, int precision, int mode)
 {
-    if (precision == WD_MIXED)
-        return mode == MODE_FT ? resident_blocks<true, MODE_FT>(ctx) : resident_blocks<true, MODE_DIST>(ctx);
-    return mode == MODE_FT ? resident_blocks<false, MODE_FT>(ctx) : resident_blocks<false, MODE_DIST>(ctx);
+    if (precision == WD_MIXED) {
+        if (mode == MODE_FT) return resident_blocks<true, MODE_FT>(ctx);
+        if (mode == MODE_RESID) return resident_blocks<true, MODE_RESID>(ctx);
+        return resident_blocks<true, MODE_DIST>(ctx);
+    }
+    if (mode == MODE_FT) return resident_blocks<false, MODE_FT>(ctx);
+    if (mode == MODE_RESID) return resident_blocks<false, MODE_RESID>(ctx);
+    return resident_blocks<false, MODE_DIST>(ctx);
 }
 
 }  // namespace
@@ -666,9 +675,11 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
     if (plan.n_items == 0) return WD_OK;
     if (precision == WD_MIXED) {
         if (mode == MODE_FT) pair_kernel<true, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        else if (mode == MODE_RESID) pair_kernel<true, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else pair_kernel<true, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
     } else {
         if (mode == MODE_FT) pair_kernel<false, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        else if (mode == MODE_RESID) pair_kernel<false, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else pair_kernel<false, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
     }
     ctx->launches++;
