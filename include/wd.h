@@ -191,6 +191,56 @@ wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule, const double* d
  * points). Used to report launch counts. */
 int64_t wd_launch_count(const wd_ctx* ctx);
 
+/* ------------------------------------------------------------ serving */
+
+/* Continuous batching of distance queries (mesh vs the unit sphere) on one GPU.
+ * Not in the paper, which times single evaluations (Sec. 4.3); this serves many
+ * queries of uneven size at once. A worker thread admits queued queries while
+ * request slots and a fixed device memory arena allow, and replays one captured
+ * CUDA graph per launch: every launch evaluates a budget of (query, node-block)
+ * items drawn round-robin from all admitted queries, so queries that arrive
+ * while others run join the next launch and short ones are not held behind long
+ * ones. Results equal those of wd_distance_dev with the same rule and precision
+ * (same kernels, same summation order per node and per block). */
+#define WD_SERVE_MAX_SLOTS 256
+
+typedef struct wd_server wd_server;
+
+typedef struct {
+    int64_t mem_cap_bytes;     /* device arena for admitted queries (meshes, records, partials) */
+    int max_slots;             /* queries admitted at once, 1..WD_SERVE_MAX_SLOTS */
+    int max_pending;           /* queue length at which submit returns WD_EBUSY */
+    int timeout_ms;            /* a query still queued after this long ends with WD_ETIMEOUT (0: never) */
+    int precision;             /* WD_FP64 or WD_MIXED */
+    int64_t pairs_per_launch;  /* (triangle, node) pairs per batched launch */
+    int n_rules;               /* 1..4 frequency rules, selected per query by R */
+    wd_rule_desc rules[4];
+} wd_serve_config;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rejected, timeouts, cancelled, failed, launches;
+    int64_t pending, active, arena_used_bytes;
+    double pairs;              /* pairs evaluated */
+    double p50_us, p99_us, max_us, mean_us;  /* submit-to-result latency of completed queries */
+    double qps;                /* completed queries per second, first submit to last result */
+    double gpu_busy;           /* fraction of that span with a batched launch in flight */
+} wd_serve_stats_t;
+
+/* Start the worker; builds the rules and captures the graph. */
+wd_status wd_serve_start(wd_ctx* ctx, const wd_serve_config* cfg, wd_server** out);
+/* Queue a query (the mesh is copied). WD_EBUSY: queue full; WD_ENOMEM: larger
+ * than the arena; WD_EINVAL: bad mesh, s <= 0 or no rule for R. */
+wd_status wd_serve_submit(wd_server* sv, const wd_mesh* mesh, double s, double R, uint64_t* ticket);
+/* Non-blocking: done = 1 once the query finished (req_status tells how). */
+wd_status wd_serve_poll(wd_server* sv, uint64_t ticket, int* done, double* dist2, wd_status* req_status);
+/* Blocks for at most timeout_ms; WD_ETIMEOUT if the query is not finished by then. */
+wd_status wd_serve_wait(wd_server* sv, uint64_t ticket, int timeout_ms, double* dist2);
+/* Cancel a queued or running query; it finishes with WD_ECANCELLED. */
+wd_status wd_serve_cancel(wd_server* sv, uint64_t ticket);
+wd_status wd_serve_stats(wd_server* sv, wd_serve_stats_t* out);
+/* Cancel queued queries, let admitted ones finish, free everything. */
+wd_status wd_serve_stop(wd_server* sv);
+
 /* ------------------------------------------------------------ allocation-free variant */
 
 /* Fixed size of the library's static device scratch used below (64 MiB). */

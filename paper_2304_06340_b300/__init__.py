@@ -48,6 +48,21 @@ class wd_measure(ctypes.Structure):
                 ("mesh", ctypes.POINTER(wd_mesh))]
 
 
+WD_SERVE_MAX_SLOTS = 256
+
+
+class wd_serve_config(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", _i64), ("max_slots", ctypes.c_int), ("max_pending", ctypes.c_int),
+                ("timeout_ms", ctypes.c_int), ("precision", ctypes.c_int), ("pairs_per_launch", _i64),
+                ("n_rules", ctypes.c_int), ("rules", wd_rule_desc * 4)]
+
+
+class wd_serve_stats_t(ctypes.Structure):
+    _fields_ = [(k, _i64) for k in ("submitted", "admitted", "completed", "rejected", "timeouts", "cancelled",
+                                    "failed", "launches", "pending", "active", "arena_used_bytes")] + \
+               [(k, ctypes.c_double) for k in ("pairs", "p50_us", "p99_us", "max_us", "mean_us", "qps", "gpu_busy")]
+
+
 def _sig(name, args, res=ctypes.c_int):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -77,6 +92,14 @@ _sig("wd_distance_grad", [_vp, _vp, ctypes.POINTER(wd_mesh), ctypes.POINTER(wd_m
 _sig("wd_distance_grad_dev", [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(wd_measure), ctypes.c_double,
                               ctypes.c_int, _vp, _vp, _vp])
 _sig("wd_launch_count", [_vp], _i64)
+_sig("wd_serve_start", [_vp, ctypes.POINTER(wd_serve_config), ctypes.POINTER(_vp)])
+_sig("wd_serve_submit", [_vp, ctypes.POINTER(wd_mesh), ctypes.c_double, ctypes.c_double,
+                         ctypes.POINTER(ctypes.c_uint64)])
+_sig("wd_serve_poll", [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), _dp, ctypes.POINTER(ctypes.c_int)])
+_sig("wd_serve_wait", [_vp, ctypes.c_uint64, ctypes.c_int, _dp])
+_sig("wd_serve_cancel", [_vp, ctypes.c_uint64])
+_sig("wd_serve_stats", [_vp, ctypes.POINTER(wd_serve_stats_t)])
+_sig("wd_serve_stop", [_vp])
 _sig("wd_distance_dev_noalloc", [_vp, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_double, ctypes.c_double, _dp,
                                  ctypes.c_int, _vp, _vp])
 
@@ -279,6 +302,62 @@ def wd_distance_dev_noalloc(xi_soa, w_geom, verts, tris, s, radius, center, prec
     _check(_lib.wd_distance_dev_noalloc(_dev_ptr(xi_soa), _dev_ptr(w_geom), w_geom.shape[0], _dev_ptr(verts),
                                         verts.shape[0], _dev_ptr(tris), tris.shape[0], float(s), float(radius),
                                         c.ctypes.data_as(_dp), int(precision), _dev_ptr(out), _stream(stream)))
+
+
+# ------------------------------------------------------------------ serving
+def wd_serve_start(ctx, rules, precision=WD_MIXED, mem_cap_bytes=8 << 30, max_slots=64, max_pending=4096,
+                   timeout_ms=0, pairs_per_launch=4_000_000_000):
+    """rules: list of (R, n_r, n_polar, n_azim, hermitian) tuples (at most 4)."""
+    cfg = wd_serve_config()
+    cfg.mem_cap_bytes = int(mem_cap_bytes)
+    cfg.max_slots = int(max_slots)
+    cfg.max_pending = int(max_pending)
+    cfg.timeout_ms = int(timeout_ms)
+    cfg.precision = int(precision)
+    cfg.pairs_per_launch = int(pairs_per_launch)
+    cfg.n_rules = len(rules)
+    for i, (R, n_r, n_p, n_a, herm) in enumerate(rules):
+        cfg.rules[i] = wd_rule_desc(WD_RULE_BALL, float(R), int(n_r), int(n_p), int(n_a), int(bool(herm)))
+    h = _vp()
+    _check(_lib.wd_serve_start(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def wd_serve_submit(server, verts, tris, s, R):
+    """Returns a ticket; raises WDError (status WD_EBUSY, WD_ENOMEM, WD_EINVAL) on refusal."""
+    m, keep = _host_mesh(verts, tris)
+    t = ctypes.c_uint64()
+    _check(_lib.wd_serve_submit(server, ctypes.byref(m), float(s), float(R), ctypes.byref(t)))
+    return t.value
+
+
+def wd_serve_poll(server, ticket):
+    """Returns (done, dist2, status)."""
+    done = ctypes.c_int()
+    d = ctypes.c_double()
+    st = ctypes.c_int()
+    _check(_lib.wd_serve_poll(server, ticket, ctypes.byref(done), ctypes.byref(d), ctypes.byref(st)))
+    return bool(done.value), d.value, st.value
+
+
+def wd_serve_wait(server, ticket, timeout_ms=60000):
+    d = ctypes.c_double()
+    _check(_lib.wd_serve_wait(server, ticket, int(timeout_ms), ctypes.byref(d)))
+    return d.value
+
+
+def wd_serve_cancel(server, ticket):
+    _check(_lib.wd_serve_cancel(server, ticket))
+
+
+def wd_serve_stats(server):
+    st = wd_serve_stats_t()
+    _check(_lib.wd_serve_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in wd_serve_stats_t._fields_}
+
+
+def wd_serve_stop(server):
+    _check(_lib.wd_serve_stop(server))
 
 
 class Context:

@@ -232,7 +232,7 @@ extern "C" void wd_destroy(wd_ctx* ctx)
     delete ctx;
 }
 
-extern "C" int64_t wd_launch_count(const wd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+extern "C" int64_t wd_launch_count(const wd_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
 extern "C" wd_status wd_sync(wd_ctx* ctx, void* stream)
 {

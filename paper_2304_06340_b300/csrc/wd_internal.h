@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -79,7 +80,7 @@ struct wd_ctx {
     int64_t n_counters = 0;
     int* d_flags = nullptr;           // [0]: invalid-input flag, [1]: final-block counter
     double* d_scalar = nullptr;       // staging for host-variant scalar results
-    int64_t launches = 0;
+    std::atomic<int64_t> launches{0};
 };
 
 // make ctx's device current
@@ -152,6 +153,35 @@ wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n
 wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
                             const double* d_resid, const void* d_rec, int64_t nt, double* d_partial,
                             const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st);
+
+// batched serving kernel (wd_pair.cu), driven by a device descriptor table
+struct ServeReq {
+    const void* rec;        // staged triangle records
+    int64_t T;              // records
+    const double* xi;       // rule nodes (SoA)
+    int64_t n;              // nodes
+    const double* W;        // weights for this request's s
+    const double* nu;       // sphere transform (re, im)
+    double* blockD;         // per-node-block partial sums of this request
+};
+struct ServeItem {
+    int req;                // slot in the request table
+    int nb;                 // node block
+};
+struct ServeFin {
+    int req;                // slot whose node blocks are all done after this launch
+    int n_nb;
+    int out;                // result index
+};
+struct ServeTable {         // laid out in pinned host memory and copied whole per launch
+    int n_items;
+    int n_fin;
+    int pad[2];
+};
+wd_status wd_launch_serve(wd_ctx* ctx, int precision, int grid, const ServeTable* d_head,
+                          const ServeReq* d_reqs, const ServeItem* d_items, const ServeFin* d_fin,
+                          double* d_results, cudaStream_t st);
+int wd_serve_resident(wd_ctx* ctx, int precision);
 
 wd_status wd_launch_weights(wd_ctx* ctx, const double* d_xi, const double* d_wg, int64_t n,
                             double s, double* d_w, cudaStream_t st);

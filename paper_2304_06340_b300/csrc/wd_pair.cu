@@ -616,6 +616,123 @@ int resident_for(wd_ctx* ctx, int precision, int mode)
     return resident_blocks<false, MODE_DIST>(ctx);
 }
 
+// ------------------------------------------------------------------ batched serving kernel
+// One work item = one node block (256 nodes) of one request, over all of that
+// request's triangles; the epilogue subtracts the sphere, weights and writes the
+// block's partial sum. Items of many requests run in the same launch, read from
+// a descriptor table in device memory. The summation order per node and per
+// block is the same as in pair_kernel with one triangle chunk, so a request's
+// result does not depend on what else is in the batch.
+template <bool MIXED>
+__global__ void __launch_bounds__(WD_NPB) serve_kernel(const ServeTable* __restrict__ head,
+                                                       const ServeReq* __restrict__ reqs,
+                                                       const ServeItem* __restrict__ items)
+{
+    using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
+    __shared__ __align__(16) Rec tile[WD_TILE];
+    __shared__ double red[WD_NPB / 32];
+    __shared__ TabEntry etab[kTab];
+    if (MIXED) fill_exp_table(etab);
+    const int n_items = head->n_items;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const ServeItem item = items[it];
+        const ServeReq rq = reqs[item.req];
+        const int64_t n = rq.n;
+        const int64_t node = (int64_t)item.nb * WD_NPB + threadIdx.x;
+        const bool active = node < n;
+        const double x = active ? rq.xi[node] : 0.0;
+        const double y = active ? rq.xi[n + node] : 0.0;
+        const double z = active ? rq.xi[2 * n + node] : 0.0;
+        NodeD qd{x, y, z};
+        NodeF qf;
+        if (MIXED) {
+            const double inv2pi = 0.15915494309189533576888376337251;
+            const double X = x * inv2pi, Y = y * inv2pi, Z = z * inv2pi;
+            qf.x = (float)x;
+            qf.y = (float)y;
+            qf.z = (float)z;
+            qf.hx = (float)X;
+            qf.hy = (float)Y;
+            qf.hz = (float)Z;
+            qf.lx = (float)(X - (double)qf.hx);
+            qf.ly = (float)(Y - (double)qf.hy);
+            qf.lz = (float)(Z - (double)qf.hz);
+            qf.dith = node_dither(node);
+        }
+        double acc_r = 0.0, acc_i = 0.0;
+        for (int64_t tb = 0; tb < rq.T; tb += WD_TILE) {
+            const int cnt = (int)((rq.T - tb) < WD_TILE ? (rq.T - tb) : WD_TILE);
+            const int cnt4 = MIXED ? ((cnt + 3) & ~3) : cnt;
+            __syncthreads();
+            {
+                const uint4* src = reinterpret_cast<const uint4*>(static_cast<const Rec*>(rq.rec) + tb);
+                uint4* dst = reinterpret_cast<uint4*>(tile);
+                const int nvec = cnt * (int)(sizeof(Rec) / 16);
+                const int nvec4 = cnt4 * (int)(sizeof(Rec) / 16);
+                for (int i = threadIdx.x; i < nvec4; i += WD_NPB)
+                    dst[i] = i < nvec ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            __syncthreads();
+            if (MIXED) {
+                Kahan kr, ki;
+                for (int j = 0; j < cnt4; j += 4) {
+                    float br = 0.0f, bi = 0.0f;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        float fr, fi;
+                        pair_mixed(etab, qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
+                        br += fr;
+                        bi += fi;
+                    }
+                    kr.add(br);
+                    ki.add(bi);
+                }
+                acc_r += kr.value();
+                acc_i += ki.value();
+            } else {
+                for (int j = 0; j < cnt; ++j) {
+                    double fr, fi;
+                    pair_f64(qd, reinterpret_cast<const TriRecD*>(tile)[j], fr, fi);
+                    acc_r += fr;
+                    acc_i += fi;
+                }
+            }
+        }
+        double mr = acc_r, mi = acc_i;
+        if (MIXED) {
+            double sd, cd;
+            sincospi(2.0 * (double)qf.dith, &sd, &cd);
+            const double r_ = mr * cd + mi * sd;
+            mi = mi * cd - mr * sd;
+            mr = r_;
+        }
+        double term = 0.0;
+        if (active) {
+            const double dr = mr - rq.nu[2 * node], di = mi - rq.nu[2 * node + 1];
+            term = rq.W[node] * (dr * dr + di * di);
+        }
+        const double bsum = block_sum(term, red);
+        if (threadIdx.x == 0) rq.blockD[item.nb] = bsum;
+    }
+}
+
+// Fixed-order sum of the block partials of every request that completes in
+// this launch (one block per request).
+__global__ void serve_finalize(const ServeTable* __restrict__ head, const ServeReq* __restrict__ reqs,
+                               const ServeFin* __restrict__ fin, double* __restrict__ results)
+{
+    __shared__ double red[WD_NPB / 32];
+    for (int f = blockIdx.x; f < head->n_fin; f += gridDim.x) {
+        const ServeFin e = fin[f];
+        const double* bd = reqs[e.req].blockD;
+        double v = 0.0;
+        for (int i = threadIdx.x; i < e.n_nb; i += WD_NPB) v += bd[i];
+        const double tot = block_sum(v, red);
+        if (threadIdx.x == 0) results[e.out] = tot;
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 size_t wd_tri_record_bytes(int precision)
@@ -684,5 +801,36 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
     }
     ctx->launches++;
     WD_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int wd_serve_resident(wd_ctx* ctx, int precision)
+{
+    static int cached[2][64] = {{0}};
+    int& c = cached[precision == WD_MIXED ? 1 : 0][ctx->device & 63];
+    if (c == 0) {
+        int per_sm = 0;
+        cudaError_t e = precision == WD_MIXED
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel<true>, WD_NPB, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel<false>, WD_NPB, 0);
+        if (e != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        c = per_sm * ctx->num_sms;
+    }
+    return c;
+}
+
+wd_status wd_launch_serve(wd_ctx* ctx, int precision, int grid, const ServeTable* d_head,
+                          const ServeReq* d_reqs, const ServeItem* d_items, const ServeFin* d_fin,
+                          double* d_results, cudaStream_t st)
+{
+    if (precision == WD_MIXED) serve_kernel<true><<<grid, WD_NPB, 0, st>>>(d_head, d_reqs, d_items);
+    else serve_kernel<false><<<grid, WD_NPB, 0, st>>>(d_head, d_reqs, d_items);
+    WD_CUDA(cudaGetLastError());
+    serve_finalize<<<ctx->num_sms, WD_NPB, 0, st>>>(d_head, d_reqs, d_fin, d_results);
+    WD_CUDA(cudaGetLastError());
+    ctx->launches += 2;
     return WD_OK;
 }
