@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-check", action="store_true", help="skip the mixed-vs-fp64 accuracy check")
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     p.add_argument("--only-n", type=int, default=None, help="restrict the sweep to one mesh (profiling runs)")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-queries", type=int, default=2000)
     return p.parse_args()
 
 
@@ -180,6 +182,57 @@ def cpu_baseline(R, queries, seconds):
     return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "long-double oracle distance, first query's mesh (%d triangles) on every %d-th node "
                       "of the rule (%d nodes, %.3g pairs, %.1f s)" % (len(t), stride, len(idx), pairs, dt)}
+
+
+def serve_bench(wd, ctx, n_queries, rate=500.0):
+    """Open-loop Poisson stream through the continuous-batching server (mixed),
+    against the plain one-query-per-launch float64 path on a sample."""
+    stream = synth.serve_stream(n_queries=n_queries, rate=rate, seed=0)
+    rules = [(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian) for R in synth.SERVE_RULES.values()]
+    sv = wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, mem_cap_bytes=16 << 30, max_slots=64,
+                           max_pending=n_queries + 16, pairs_per_launch=4_000_000_000)
+    try:
+        for q in stream[:4]:  # warm-up: weight caches, first launches
+            wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
+        # service time: one query in flight at a time
+        svc = []
+        for q in stream[4:24]:
+            t0 = time.perf_counter()
+            wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
+            svc.append(1e3 * (time.perf_counter() - t0))
+        wd.wd_serve_stop(sv)
+        sv = wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, mem_cap_bytes=16 << 30, max_slots=64,
+                               max_pending=n_queries + 16, pairs_per_launch=4_000_000_000)
+        for q in stream[:4]:
+            wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
+        launches0 = ctx.launches()
+        t_start = time.perf_counter()
+        tickets = []
+        for q in stream:  # open loop: submit at the arrival times
+            delay = q.arrival_s - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R))
+        served = [wd.wd_serve_wait(sv, tk, 3600000) for tk in tickets]
+        st = wd.wd_serve_stats(sv)
+    finally:
+        wd.wd_serve_stop(sv)
+    # plain float64 path, one query per call, on a sample of the stream
+    sample = stream[:6]
+    rule_of = {R: ctx.rule(*next(r for r in rules if r[0] == R)) for R in synth.SERVE_RULES}
+    t0 = time.perf_counter()
+    ref = [ctx.distance(rule_of[q.R], q.verts, q.tris, None, q.s, wd.WD_FP64) for q in sample]
+    fp64_qps = len(sample) / (time.perf_counter() - t0)
+    errs = [abs(a - b) / b for a, b in zip(served[:len(sample)], ref)]
+    return {"queries": n_queries, "offered_qps": rate, "achieved_qps": st["qps"],
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+            "latency_note": "open loop, submit to result, queueing included",
+            "service_ms_p50": statistics.median(svc), "service_ms_max": max(svc),
+            "fp64_one_per_launch_qps": fp64_qps, "speedup_vs_fp64_one_per_launch": st["qps"] / fp64_qps,
+            "max_rel_err_vs_fp64": max(errs), "fp64_sample": len(sample),
+            "launches": st["launches"], "gpu_kernel_launches": ctx.launches() - launches0,
+            "gpu_busy": st["gpu_busy"], "pairs": st["pairs"], "completed": st["completed"],
+            "rules": ["R=%g %dx%dx%d%s" % (r[0], r[1], r[2], r[3], " herm" if r[4] else "") for r in rules]}
 
 
 def run_reference(args, cfg, queries, R):
@@ -352,6 +405,9 @@ def main():
                              N_MUFU_PER_PAIR)}
     if prec == wd.WD_FP64:
         roof["note"] = "float64 path: bounded by the FP64 pipe, not by the FP32/MUFU roofline shown"
+    serve = None
+    if world == 1 and not args.no_serve and args.only_n is None:
+        serve = serve_bench(wd, ctx, args.serve_queries)
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(R, queries, args.cpu_sample_seconds)
@@ -365,7 +421,7 @@ def main():
             "query_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                  "max": lat[-1], "note": "per-query kernel time, back-to-back queries"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "accuracy": accuracy, "distances": d_values[:len(dq)]}
+            "accuracy": accuracy, "distances": d_values[:len(dq)], "serve": serve}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
