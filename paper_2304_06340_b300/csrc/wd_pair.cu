@@ -196,7 +196,7 @@ struct NodeF {
     float x, y, z;     // xi (radians), float32
     float hx, hy, hz;  // xi / 2 pi, high float32 part
     float lx, ly, lz;  // xi / 2 pi - high part
-    float dith;        // per-node phase origin shift in turns, [0, 1)
+    float dith;        // per-node phase origin shift in turns, [-1/2, 1/2)
 };
 
 // Per-node phase dither. The float32 rounding of each pair's terms is a
@@ -207,6 +207,12 @@ struct NodeF {
 // rotating the node's sum back by exp(-2 pi i d_k) in float64 leaves the
 // result unchanged (translation theorem) while making the rounding errors of
 // different nodes independent, so they average out in the quadrature sum.
+// The shift lies in [-1/2, 1/2) on a 2^-20 grid: the reduced phase f is in
+// [-1/2, 1/2], so f - d stays below 1 in magnitude, and when f itself lies on
+// a coarse grid (large high products, e.g. a frequency component exactly 0)
+// f - d is exact. A shift in [0, 1) would push half the phases past 1, where
+// rounding to the 2^-23 grid depends on d's last bit alone, the same for every
+// triangle of the node: a coherent phase error.
 __device__ __forceinline__ float node_dither(int64_t node)
 {
     uint32_t h = (uint32_t)node * 0x9E3779B9u + 0x7F4A7C15u;
@@ -215,7 +221,7 @@ __device__ __forceinline__ float node_dither(int64_t node)
     h ^= h >> 13;
     h *= 0xC2B2AE35u;
     h ^= h >> 16;
-    return (float)(h >> 8) * 5.9604644775390625e-8f;  // 24 bits, exact in float32
+    return (float)(h >> 12) * 9.5367431640625e-7f - 0.5f;  // 20 bits, exact in float32
 }
 
 // sin(x)/x: reduction by the nearest multiple of pi (two-constant split) and
