@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "wd_internal.h"
+#include "wd_math.cuh"
 
 namespace {
 
@@ -237,6 +238,272 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_f64(const double* __re
     }
 }
 
+// ------------------------------------------------------------------ mixed adjoint
+// The same quantities in float32 arithmetic with the forward mixed path's
+// safeguards: centroid phase in turns from float pairs, a per-node phase
+// dither (undone by rotating the node's residual by exp(2 pi i d)), the
+// table-driven exp(-i theta), the Taylor series in Horner form together with
+// its p and q derivatives, and separate accumulators for the exact 1/2 part of
+// Psi, so that the tail is never rounded against it. Per-node-tile sums are
+// float32, flushed to float64.
+constexpr float kDeltaAM = 3.0f;
+
+struct AdjNodeF {
+    NodeF q;
+    float rr, ri;  // residual times exp(2 pi i d)
+};
+
+// sinc(h) and sinc'(h) in float32: their Taylor series below |h| = 1
+// (remainders < 1e-12); otherwise sin r and cos r from Taylor polynomials
+// after reducing h by the nearest multiple of pi, r = h - k pi with a
+// two-constant split of pi, |r| <= pi/2 (remainders < 1e-9)
+__device__ __forceinline__ void sincd32(float h, float& sc, float& dsc)
+{
+    const float h2 = h * h;
+    if (fabsf(h) < 1.0f) {
+        float a = fmaf(h2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+        a = fmaf(a, h2, 1.0f / 362880.0f);
+        a = fmaf(a, h2, -1.0f / 5040.0f);
+        a = fmaf(a, h2, 1.0f / 120.0f);
+        a = fmaf(a, h2, -1.0f / 6.0f);
+        sc = fmaf(a, h2, 1.0f);
+        float b = fmaf(h2, 1.0f / 518918400.0f, -1.0f / 3991680.0f);
+        b = fmaf(b, h2, 1.0f / 45360.0f);
+        b = fmaf(b, h2, -1.0f / 840.0f);
+        b = fmaf(b, h2, 1.0f / 30.0f);
+        b = fmaf(b, h2, -1.0f / 3.0f);
+        dsc = b * h;
+        return;
+    }
+    const float k = rintf(h * 0.318309886183790672f);
+    float r = fmaf(-k, 3.14159274101257324f, h);
+    r = fmaf(-k, -8.74227766e-8f, r);
+    const float r2 = r * r;
+    float sp = fmaf(r2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+    sp = fmaf(sp, r2, 1.0f / 362880.0f);
+    sp = fmaf(sp, r2, -1.0f / 5040.0f);
+    sp = fmaf(sp, r2, 1.0f / 120.0f);
+    sp = fmaf(sp, r2, -1.0f / 6.0f);
+    const float sr = fmaf(r * r2, sp, r);
+    float cp = fmaf(r2, -1.0f / 87178291200.0f, 1.0f / 479001600.0f);
+    cp = fmaf(cp, r2, -1.0f / 3628800.0f);
+    cp = fmaf(cp, r2, 1.0f / 40320.0f);
+    cp = fmaf(cp, r2, -1.0f / 720.0f);
+    cp = fmaf(cp, r2, 1.0f / 24.0f);
+    cp = fmaf(cp, r2, -0.5f);
+    const float cr = fmaf(cp, r2, 1.0f);
+    const float half = 0.5f * k;
+    const float sgn = (half == rintf(half)) ? 1.0f : -1.0f;
+    const float inv = 1.0f / h;
+    sc = sgn * sr * inv;
+    dsc = (sgn * cr - sc) * inv;
+}
+
+__global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __restrict__ xi, int64_t n,
+                                                                const double* __restrict__ resid,
+                                                                const TriRecF* __restrict__ rec, int64_t nt,
+                                                                const AdjPlan p, double* __restrict__ partial)
+{
+    __shared__ AdjNodeF sn[ADJ_NPT];
+    __shared__ TabEntry etab[kTab];
+    fill_exp_table(etab);
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const int64_t tb = item / p.nchunks;
+        const int chunk = (int)(item - tb * p.nchunks);
+        const int64_t tri = tb * ADJ_TPB + threadIdx.x;
+        const bool active = tri < nt;
+        TriRecF t{};
+        if (active) t = rec[tri];
+        // float64 totals: 1/2-part and tail of rho_0, of rho_i xi, and rho_1 xi, rho_2 xi
+        double A0h = 0.0, A0t = 0.0, Aih[3] = {0, 0, 0}, Ait[3] = {0, 0, 0}, A1[3] = {0, 0, 0}, A2[3] = {0, 0, 0};
+        const int64_t k0 = (int64_t)chunk * p.tiles_per_chunk * ADJ_NPT;
+        int64_t k1 = k0 + (int64_t)p.tiles_per_chunk * ADJ_NPT;
+        if (k1 > n) k1 = n;
+        for (int64_t kb = k0; kb < k1; kb += ADJ_NPT) {
+            const int cnt = (int)((k1 - kb) < ADJ_NPT ? (k1 - kb) : ADJ_NPT);
+            __syncthreads();
+            for (int i = threadIdx.x; i < cnt; i += ADJ_TPB) {
+                const int64_t k = kb + i;
+                const double x = xi[k], y = xi[n + k], z = xi[2 * n + k];
+                const double inv2pi = 0.15915494309189533576888376337251;
+                const double X = x * inv2pi, Y = y * inv2pi, Z = z * inv2pi;
+                AdjNodeF a;
+                a.q.x = (float)x;
+                a.q.y = (float)y;
+                a.q.z = (float)z;
+                a.q.hx = (float)X;
+                a.q.hy = (float)Y;
+                a.q.hz = (float)Z;
+                a.q.lx = (float)(X - (double)a.q.hx);
+                a.q.ly = (float)(Y - (double)a.q.hy);
+                a.q.lz = (float)(Z - (double)a.q.hz);
+                a.q.dith = node_dither(k);
+                double sd, cd;
+                sincospi(2.0 * (double)a.q.dith, &sd, &cd);
+                const double r0 = resid[2 * k], r1 = resid[2 * k + 1];
+                a.rr = (float)(r0 * cd - r1 * sd);
+                a.ri = (float)(r0 * sd + r1 * cd);
+                sn[i] = a;
+            }
+            __syncthreads();
+            if (!active) continue;
+            float b0h = 0.0f, b0t = 0.0f, bih[3] = {0, 0, 0}, bit[3] = {0, 0, 0}, b1[3] = {0, 0, 0}, b2[3] = {0, 0, 0};
+            for (int kk = 0; kk < cnt; ++kk) {
+                const AdjNodeF& a = sn[kk];
+                const NodeF& q = a.q;
+                // centroid phase in turns (as in the forward mixed pair), dithered
+                const float p0 = q.hx * t.mh[0], p1 = q.hy * t.mh[1], p2 = q.hz * t.mh[2];
+                const float e0 = fmaf(q.hx, t.mh[0], -p0);
+                const float e1 = fmaf(q.hy, t.mh[1], -p1);
+                const float e2 = fmaf(q.hz, t.mh[2], -p2);
+                float f = (p0 - rintf(p0)) + (p1 - rintf(p1));
+                f -= rintf(f);
+                f += p2 - rintf(p2);
+                f -= rintf(f);
+                float lo = e0 + e1 + e2;
+                lo = fmaf(q.hx, t.ml[0], lo);
+                lo = fmaf(q.hy, t.ml[1], lo);
+                lo = fmaf(q.hz, t.ml[2], lo);
+                lo = fmaf(q.lx, t.mh[0], lo);
+                lo = fmaf(q.ly, t.mh[1], lo);
+                lo = fmaf(q.lz, t.mh[2], lo);
+                const float tau = f - q.dith;
+                const float g1 = fmaf(q.x, t.e1[0], fmaf(q.y, t.e1[1], q.z * t.e1[2]));
+                const float g2 = fmaf(q.x, t.e2[0], fmaf(q.y, t.e2[1], q.z * t.e2[2]));
+                const float g3 = g2 - g1;
+                const float a1 = fabsf(g1), a2 = fabsf(g2), a3 = fabsf(g3);
+                const float gmax = fmaxf(a1, fmaxf(a2, a3));
+                const float ya = -(g1 + g2) * (1.0f / 3.0f);
+                const float yb = (2.0f * g1 - g2) * (1.0f / 3.0f);
+                const float yc = (2.0f * g2 - g1) * (1.0f / 3.0f);
+                const float rr = a.rr, ri = a.ri;
+                float rho0h = 0.0f, rho0t, rhoih = 0.0f, rhoit, rho1, rho2;
+                if (gmax < kDeltaAM) {
+                    const float pp = (g1 * g1 - g1 * g2 + g2 * g2) * (1.0f / 3.0f);
+                    const float qq = ya * yb * yc;
+                    const float A = fmaf(g1, g1 - g2, g2 * g2);
+                    const float q2 = qq * qq;
+                    // tail = Psi - 1/2 (as in the forward pass)
+                    float re = fmaf(pp, 1.0f / 87178291200.0f, -1.0f / 479001600.0f);
+                    re = fmaf(re, pp, 1.0f / 3628800.0f);
+                    re = fmaf(re, pp, -1.0f / 40320.0f);
+                    re = fmaf(re, pp, 1.0f / 720.0f);
+                    float rq = fmaf(pp, 10.0f / 87178291200.0f, -6.0f / 479001600.0f);
+                    rq = fmaf(rq, pp, 3.0f / 3628800.0f);
+                    rq = fmaf(rq, pp, -1.0f / 40320.0f);
+                    const float rq4 = fmaf(q2, 1.0f / 87178291200.0f, rq);
+                    float sr = fmaf(re, pp * pp, q2 * rq4);
+                    sr = fmaf(A, -1.388888899e-02f, fmaf(A, 1.034802868e-10f, sr));
+                    float im = fmaf(pp, 5.0f / 6227020800.0f, -4.0f / 39916800.0f);
+                    im = fmaf(im, pp, 3.0f / 362880.0f);
+                    im = fmaf(im, pp, -2.0f / 5040.0f);
+                    im = fmaf(im, pp, 1.0f / 120.0f);
+                    const float iq = fmaf(pp, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
+                    const float si = qq * fmaf(q2, iq, im);
+                    // d tail / dp and d tail / dq
+                    float dre = fmaf(pp, 6.0f / 87178291200.0f, -5.0f / 479001600.0f);
+                    dre = fmaf(dre, pp, 4.0f / 3628800.0f);
+                    dre = fmaf(dre, pp, -3.0f / 40320.0f);
+                    dre = fmaf(dre, pp, 2.0f / 720.0f);
+                    float drq = fmaf(pp, 30.0f / 87178291200.0f, -12.0f / 479001600.0f);
+                    drq = fmaf(drq, pp, 3.0f / 3628800.0f);
+                    const float Ppr = fmaf(dre, pp, fmaf(q2, drq, -1.0f / 24.0f));
+                    const float Pqr = qq * fmaf(2.0f, rq, 4.0f * q2 / 87178291200.0f);
+                    float dim = fmaf(pp, 20.0f / 6227020800.0f, -12.0f / 39916800.0f);
+                    dim = fmaf(dim, pp, 6.0f / 362880.0f);
+                    dim = fmaf(dim, pp, -2.0f / 5040.0f);
+                    const float Ppi = qq * fmaf(q2, 4.0f / 6227020800.0f, dim);
+                    const float Pqi = fmaf(3.0f * q2, iq, im);
+                    // dq/dg1, dq/dg2; dp/dg1 = y_b, dp/dg2 = y_c
+                    const float dq1 = (-yb * yc + 2.0f * ya * yc - ya * yb) * (1.0f / 3.0f);
+                    const float dq2 = (-yb * yc - ya * yc + 2.0f * ya * yb) * (1.0f / 3.0f);
+                    const float P1r = fmaf(Ppr, yb, Pqr * dq1), P1i = fmaf(Ppi, yb, Pqi * dq1);
+                    const float P2r = fmaf(Ppr, yc, Pqr * dq2), P2i = fmaf(Ppi, yc, Pqi * dq2);
+                    float c, s;
+                    expm_turns(etab, tau, lo, c, s);  // exp(-i (t_m - 2 pi d)) = (c, s)
+                    // Z = conj(r') E
+                    const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
+                    rho0h = Zr;
+                    rho0t = fmaf(Zr, sr, -Zi * si);
+                    rhoih = Zi;
+                    rhoit = fmaf(Zr, si, Zi * sr);
+                    // Re(Z P1), Re(Z P2)
+                    rho1 = fmaf(Zr, P1r, -Zi * P1i);
+                    rho2 = fmaf(Zr, P2r, -Zi * P2i);
+                } else {
+                    const bool caseA = (a2 >= a1) && (a2 >= a3);
+                    const bool caseB = !caseA && (a1 >= a3);
+                    float oP1, oP2, hP1, hP2, oQ1, oQ2, hQ1, hQ2, D, D1, D2;
+                    if (caseA) {
+                        oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
+                        oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
+                        D = g2; D1 = 0.0f; D2 = 1.0f;
+                    } else if (caseB) {
+                        oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
+                        oQ1 = -1.0f / 3; oQ2 = 1.0f / 6; hQ1 = 0.0f; hQ2 = 0.5f;
+                        D = g1; D1 = 1.0f; D2 = 0.0f;
+                    } else {
+                        oP1 = -1.0f / 3; oP2 = 1.0f / 6; hP1 = 0.0f; hP2 = 0.5f;
+                        oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
+                        D = g3; D1 = -1.0f; D2 = 1.0f;
+                    }
+                    const float offP = oP1 * g1 + oP2 * g2, hP = hP1 * g1 + hP2 * g2;
+                    const float offQ = oQ1 * g1 + oQ2 * g2, hQ = hQ1 * g1 + hQ2 * g2;
+                    const float inv2pif = 0.159154943091895336f;
+                    float cP, sP, cQ, sQ;
+                    expm_turns(etab, tau + offP * inv2pif, lo, cP, sP);
+                    expm_turns(etab, tau + offQ * inv2pif, lo, cQ, sQ);
+                    float scP, dscP, scQ, dscQ;
+                    sincd32(hP, scP, dscP);
+                    sincd32(hQ, scQ, dscQ);
+                    const float SPr = cP * scP, SPi = sP * scP, SQr = cQ * scQ, SQi = sQ * scQ;
+                    const float inv = 1.0f / D;
+                    const float Gr = -(SPi - SQi) * inv, Gi = (SPr - SQr) * inv;
+                    // dS/dg = S (-i doff) + E sinc' dh ; -i o S = o (S.i, -S.r)
+                    const float dP1r = fmaf(SPi, oP1, cP * dscP * hP1), dP1i = fmaf(-SPr, oP1, sP * dscP * hP1);
+                    const float dP2r = fmaf(SPi, oP2, cP * dscP * hP2), dP2i = fmaf(-SPr, oP2, sP * dscP * hP2);
+                    const float dQ1r = fmaf(SQi, oQ1, cQ * dscQ * hQ1), dQ1i = fmaf(-SQr, oQ1, sQ * dscQ * hQ1);
+                    const float dQ2r = fmaf(SQi, oQ2, cQ * dscQ * hQ2), dQ2i = fmaf(-SQr, oQ2, sQ * dscQ * hQ2);
+                    // V = (i (dS_P - dS_Q) - G dD) / D (already including the phase factor)
+                    const float V1r = (-(dP1i - dQ1i) - Gr * D1) * inv, V1i = ((dP1r - dQ1r) - Gi * D1) * inv;
+                    const float V2r = (-(dP2i - dQ2i) - Gr * D2) * inv, V2i = ((dP2r - dQ2r) - Gi * D2) * inv;
+                    rho0t = fmaf(rr, Gr, ri * Gi);
+                    rhoit = fmaf(rr, Gi, -ri * Gr);  // 3 rho_i
+                    rho1 = fmaf(rr, V1r, ri * V1i);
+                    rho2 = fmaf(rr, V2r, ri * V2i);
+                }
+                const float xs[3] = {q.x, q.y, q.z};
+                b0h += rho0h;
+                b0t += rho0t;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    bih[c] = fmaf(rhoih, xs[c], bih[c]);
+                    bit[c] = fmaf(rhoit, xs[c], bit[c]);
+                    b1[c] = fmaf(rho1, xs[c], b1[c]);
+                    b2[c] = fmaf(rho2, xs[c], b2[c]);
+                }
+            }
+            A0h += b0h;
+            A0t += b0t;
+            for (int c = 0; c < 3; ++c) {
+                Aih[c] += bih[c];
+                Ait[c] += bit[c];
+                A1[c] += b1[c];
+                A2[c] += b2[c];
+            }
+        }
+        if (active) {
+            double* o = partial + ((int64_t)chunk * nt + tri) * 10;
+            o[0] = 0.5 * A0h + A0t;
+            for (int c = 0; c < 3; ++c) {
+                o[1 + c] = (0.5 * Aih[c] + Ait[c]) * (1.0 / 3.0);
+                o[4 + c] = A1[c];
+                o[7 + c] = A2[c];
+            }
+        }
+    }
+}
+
 // Sum the node chunks per triangle (fixed order), apply d gamma/dp_j and gamma,
 // and add the three vertex contributions to grad (float64 atomics).
 __global__ void adjoint_finalize(const double* __restrict__ partial, int nchunks, const TriRecD* __restrict__ rec,
@@ -278,14 +545,16 @@ __global__ void adjoint_finalize(const double* __restrict__ partial, int nchunks
     }
 }
 
-int resident_adjoint(wd_ctx* ctx)
+int resident_adjoint(wd_ctx* ctx, int precision)
 {
-    static int cached[64] = {0};
-    int& c = cached[ctx->device & 63];
+    static int cached[2][64] = {{0}};
+    const int m = precision == WD_MIXED ? 1 : 0;
+    int& c = cached[m][ctx->device & 63];
     if (c == 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_f64, ADJ_TPB, 0) != cudaSuccess ||
-            per_sm < 1) {
+        cudaError_t e = m ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_mixed, ADJ_TPB, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_f64, ADJ_TPB, 0);
+        if (e != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
         }
@@ -296,12 +565,12 @@ int resident_adjoint(wd_ctx* ctx)
 
 }  // namespace
 
-wd_status wd_plan_adjoint(wd_ctx* ctx, int, int64_t n_nodes, int64_t n_tris, AdjPlan* plan)
+wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n_tris, AdjPlan* plan)
 {
     AdjPlan p;
     p.n_tb = (n_tris + ADJ_TPB - 1) / ADJ_TPB;
     p.n_node_tiles = (n_nodes + ADJ_NPT - 1) / ADJ_NPT;
-    const int64_t resident = resident_adjoint(ctx);
+    const int64_t resident = resident_adjoint(ctx, precision);
     const int64_t target = 4 * resident;
     int64_t nchunks = 1;
     if (p.n_tb > 0 && p.n_tb < target && p.n_node_tiles > 1) {
@@ -319,14 +588,19 @@ wd_status wd_plan_adjoint(wd_ctx* ctx, int, int64_t n_nodes, int64_t n_tris, Adj
     return WD_OK;
 }
 
-wd_status wd_launch_adjoint(wd_ctx* ctx, int, const AdjPlan& plan, const double* d_xi, int64_t n,
-                            const double* d_resid, const void* d_rec, int64_t nt, double* d_partial,
-                            const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st)
+wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
+                            const double* d_resid, const void* d_rec, const void* d_rec_mixed, int64_t nt,
+                            double* d_partial, const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st)
 {
     if (nt == 0) return WD_OK;
     if (plan.n_items > 0) {
-        adjoint_kernel_f64<<<plan.grid, ADJ_TPB, 0, st>>>(d_xi, n, d_resid, static_cast<const TriRecD*>(d_rec), nt,
-                                                         plan, d_partial);
+        if (precision == WD_MIXED)
+            adjoint_kernel_mixed<<<plan.grid, ADJ_TPB, 0, st>>>(d_xi, n, d_resid,
+                                                               static_cast<const TriRecF*>(d_rec_mixed), nt, plan,
+                                                               d_partial);
+        else
+            adjoint_kernel_f64<<<plan.grid, ADJ_TPB, 0, st>>>(d_xi, n, d_resid, static_cast<const TriRecD*>(d_rec),
+                                                             nt, plan, d_partial);
         ctx->launches++;
         WD_CUDA(cudaGetLastError());
     }

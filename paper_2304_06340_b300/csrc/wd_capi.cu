@@ -397,7 +397,8 @@ extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_me
 }
 
 // Gradient core on device pointers: forward pass in `precision` writing D and
-// the residual 2 W (mu^ - nu^), then the float64 adjoint over mu's triangles.
+// the residual 2 W (mu^ - nu^), then the adjoint in the same precision over
+// mu's triangles.
 static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const double* d_verts, int64_t nv,
                            const int32_t* d_tris, int64_t nt, const wd_measure* nu, double s, double* d_dist2,
                            double* d_grad, size_t base, cudaStream_t st)
@@ -406,7 +407,7 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     const int64_t n = rule->n_eval;
     CoreLayout L = core_layout(ctx, precision, MODE_RESID, n, nt + nt2, base);
     AdjPlan ap;
-    wd_plan_adjoint(ctx, WD_FP64, n, nt, &ap);
+    wd_plan_adjoint(ctx, precision, n, nt, &ap);
     size_t off = L.end;
     const size_t o_res = off;
     off += align_up(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
@@ -450,8 +451,8 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     // adjoint over mu's triangles, staged in float64
     void* rec64 = ctx->ws + o_rec64;
     if ((st_ = wd_launch_stage(ctx, WD_FP64, d_verts, nv, d_tris, nt, 1.0, rec64, 0, st)) != WD_OK) return st_;
-    return wd_launch_adjoint(ctx, WD_FP64, ap, rule->d_xi, n, resid, rec64, nt,
-                             reinterpret_cast<double*>(ctx->ws + o_adj), d_tris, nv, d_grad, st);
+    return wd_launch_adjoint(ctx, precision, ap, rule->d_xi, n, resid, rec64, precision == WD_MIXED ? rec : nullptr,
+                             nt, reinterpret_cast<double*>(ctx->ws + o_adj), d_tris, nv, d_grad, st);
 }
 
 extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
@@ -503,7 +504,7 @@ extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const 
         const int64_t nt2 = m2 ? m2->n_tris : 0;
         CoreLayout L = core_layout(ctx, precision, MODE_RESID, rule->n_eval, mu->n_tris + nt2, base);
         AdjPlan ap;
-        wd_plan_adjoint(ctx, WD_FP64, rule->n_eval, mu->n_tris, &ap);
+        wd_plan_adjoint(ctx, precision, rule->n_eval, mu->n_tris, &ap);
         size_t need = L.end + align_up(sizeof(double) * 2 * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1)) +
                       align_up(sizeof(TriRecD) * (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
                       align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) *

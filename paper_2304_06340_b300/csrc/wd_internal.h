@@ -150,9 +150,11 @@ struct AdjPlan {
     int grid = 0;
 };
 wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n_tris, AdjPlan* plan);
+// d_rec: float64 records of mu (geometry for the final scatter, and the
+// float64 adjoint); d_rec_mixed: mixed records of mu (mixed adjoint)
 wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
-                            const double* d_resid, const void* d_rec, int64_t nt, double* d_partial,
-                            const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st);
+                            const double* d_resid, const void* d_rec, const void* d_rec_mixed, int64_t nt,
+                            double* d_partial, const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st);
 
 // batched serving kernel (wd_pair.cu), driven by a device descriptor table
 struct ServeReq {

@@ -1,0 +1,129 @@
+// Device building blocks of the mixed-precision path, shared by the pair
+// kernels (wd_pair.cu) and the adjoint (wd_adjoint.cu).
+#pragma once
+
+#include <cstdint>
+
+struct NodeF {
+    float x, y, z;     // xi (radians), float32
+    float hx, hy, hz;  // xi / 2 pi, high float32 part
+    float lx, ly, lz;  // xi / 2 pi - high part
+    float dith;        // per-node phase origin shift in turns, [-1/2, 1/2)
+};
+
+// Per-node phase dither. The float32 rounding of each pair's terms is a
+// deterministic function of its phases; at low frequency neighbouring nodes
+// see nearly equal phases, round alike, and the per-node errors add up
+// coherently in the weighted sum against mu^ - nu^, which is small there.
+// Shifting every phase of node k by a pseudo-random turn offset d_k and
+// rotating the node's sum back by exp(-2 pi i d_k) in float64 leaves the
+// result unchanged (translation theorem) while making the rounding errors of
+// different nodes independent, so they average out in the quadrature sum.
+// The shift lies in [-1/2, 1/2) on a 2^-20 grid: the reduced phase f is in
+// [-1/2, 1/2], so f - d stays below 1 in magnitude, and when f itself lies on
+// a coarse grid (large high products, e.g. a frequency component exactly 0)
+// f - d is exact. A shift in [0, 1) would push half the phases past 1, where
+// rounding to the 2^-23 grid depends on d's last bit alone, the same for every
+// triangle of the node: a coherent phase error.
+__device__ __forceinline__ float node_dither(int64_t node)
+{
+    uint32_t h = (uint32_t)node * 0x9E3779B9u + 0x7F4A7C15u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (float)(h >> 12) * 9.5367431640625e-7f - 0.5f;  // 20 bits, exact in float32
+}
+
+// sin(x)/x: reduction by the nearest multiple of pi (two-constant split) and
+// the Taylor polynomial of sin(r)/r on |r| <= pi/2 (remainder < 5e-10).
+__device__ __forceinline__ float sinc32(float x)
+{
+    const float k = rintf(x * 0.318309886183790672f);
+    float r = fmaf(-k, 3.14159274101257324f, x);
+    r = fmaf(-k, -8.74227766e-8f, r);
+    const float r2 = r * r;
+    float P = -1.0f / 1307674368000.0f;
+    P = fmaf(P, r2, 1.0f / 6227020800.0f);
+    P = fmaf(P, r2, -1.0f / 39916800.0f);
+    P = fmaf(P, r2, 1.0f / 362880.0f);
+    P = fmaf(P, r2, -1.0f / 5040.0f);
+    P = fmaf(P, r2, 1.0f / 120.0f);
+    P = fmaf(P, r2, -1.0f / 6.0f);
+    P = fmaf(P, r2, 1.0f);
+    // sin(x) = (-1)^k r P; for k = 0, r == x exactly
+    const float half = 0.5f * k;
+    const float sgn = (half == rintf(half)) ? 1.0f : -1.0f;
+    const float qf = (k == 0.0f) ? 1.0f : __fdividef(sgn * r, x);
+    return P * qf;
+}
+
+// exp(-i 2 pi tau) for a phase in turns given as the unevaluated float pair
+// tau + tlo, without rounding 2 pi into the argument. tau = j/256 + u with j
+// the nearest multiple (found with a magic-number add, so no float-to-int
+// conversion) and |u| <= 1/512 exactly; exp(-2 pi i j/256) comes from a table
+// of float pairs (hi + lo, from float64 sincospi), exp(-i x), x = 2 pi u, from
+// short Taylor polynomials (|x| <= pi/256: remainders below 3e-12), and the
+// two are combined in pair arithmetic. Unlike a float32 polynomial on a quarter
+// turn, whose rounded coefficients bias its mean amplitude by about 1e-9,
+// this has a mean relative bias near 1e-11, which matters because the phases
+// of a node's triangles are uniformly spread and any mean bias scales mu^.
+constexpr int kTab = 256;
+struct __align__(16) TabEntry {
+    float ch, cl, sh, sl;  // cos and sin of 2 pi j / 256 as float pairs
+};
+
+__device__ __forceinline__ void fill_exp_table(TabEntry* tab)
+{
+    for (int j = threadIdx.x; j < kTab; j += blockDim.x) {
+        double sd, cd;
+        sincospi(2.0 * j / kTab, &sd, &cd);
+        TabEntry e;
+        e.ch = (float)cd;
+        e.cl = (float)(cd - (double)e.ch);
+        e.sh = (float)sd;
+        e.sl = (float)(sd - (double)e.sh);
+        tab[j] = e;
+    }
+}
+
+__device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tab, float tau, float tlo,
+                                           float& er, float& ei)
+{
+    const float magic = 12582912.0f;  // 1.5 * 2^23: rounds to an integer in the low bits
+    const float km = fmaf(tau, (float)kTab, magic);
+    const int idx = __float_as_int(km) & (kTab - 1);
+    const float k = km - magic;                   // exact
+    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/512
+    const float xh = u * 6.28318548202514648f;
+    float xl = fmaf(u, 6.28318548202514648f, -xh);
+    xl = fmaf(u, -1.74845553e-7f, xl);            // 2 pi - float(2 pi)
+    xl = fmaf(tlo, 6.28318548202514648f, xl);
+    const float x2 = xh * xh;
+    // cos x - 1 and sin x - xh
+    const float dc = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), -xh * xl);
+    const float ds = fmaf(xh * x2, -1.0f / 6.0f, xl);
+    const TabEntry t = tab[idx];
+    // cos(theta) = Tc (1 + dc) - Ts sin x, sin(theta) = Ts (1 + dc) + Tc sin x
+    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, xh, t.cl + fmaf(-t.sh, ds, -t.sl * xh)));
+    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, xh, t.sl + fmaf(t.ch, ds, t.cl * xh)));
+    er = c;   // exp(-i theta) = cos theta - i sin theta
+    ei = -s;
+}
+
+// Kahan-compensated float32 accumulation: the per-tile sum of nearly equal
+// terms at low frequency would otherwise round the same way at neighbouring
+// nodes, a coherent error that the mesh-minus-sphere difference magnifies.
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
