@@ -19,8 +19,10 @@
 // Work items are (block of 128 triangles, chunk of frequency nodes); nodes are
 // staged in shared-memory tiles; each thread keeps the ten per-triangle sums
 // sum Re(conj r G), sum rho_i xi, sum rho_1 xi, sum rho_2 xi in float64. A
-// second kernel adds the chunks in fixed order, applies the geometry and
-// scatters to the vertices with float64 atomic adds.
+// second kernel adds the chunks in fixed order and applies the geometry; a
+// third scatters the corner contributions to the vertices with float64 atomic
+// adds made exact by rounding to a per-(vertex, component) grid, so the
+// gradient has the same bits on every run.
 #include <cstdint>
 
 #include "wd_internal.h"
@@ -505,9 +507,12 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __
 }
 
 // Sum the node chunks per triangle (fixed order), apply d gamma/dp_j and gamma,
-// and add the three vertex contributions to grad (float64 atomics).
+// and store the three corner contributions. Each (vertex, component) records
+// the largest binary exponent among its contributions, and each vertex its
+// number of incident corners, for the order-independent scatter below.
 __global__ void adjoint_finalize(const double* __restrict__ partial, int nchunks, const TriRecD* __restrict__ rec,
-                                 int64_t nt, const int32_t* __restrict__ tris, int64_t nv, double* __restrict__ grad)
+                                 int64_t nt, const int32_t* __restrict__ tris, int64_t nv,
+                                 double* __restrict__ corner, int* __restrict__ expo, int* __restrict__ deg)
 {
     for (int64_t tri = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tri < nt;
          tri += (int64_t)gridDim.x * blockDim.x) {
@@ -519,7 +524,12 @@ __global__ void adjoint_finalize(const double* __restrict__ partial, int nchunks
             for (int c = 0; c < 10; ++c) S[c] += partial[((int64_t)ch * nt + tri) * 10 + c];
         const TriRecD t = rec[tri];
         const double gam = t.gam;
-        if (!(gam > 0.0)) continue;  // degenerate triangles contribute nothing
+        double* out = corner + 9 * tri;
+        if (!(gam > 0.0)) {  // degenerate triangles contribute nothing
+#pragma unroll
+            for (int c = 0; c < 9; ++c) out[c] = 0.0;
+            continue;
+        }
         const double* e1 = t.e1;
         const double* e2 = t.e2;
         double nrm[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -531,7 +541,8 @@ __global__ void adjoint_finalize(const double* __restrict__ partial, int nchunks
         const double* ev[3] = {ea, eb, ec};
         for (int j = 0; j < 3; ++j) {
             const int64_t v = tris[3 * tri + j];
-            if (v < 0 || v >= nv) continue;
+            const bool ok = v >= 0 && v < nv;
+            if (ok) atomicAdd(&deg[v], 1);
             const double* e = ev[j];
             const double dg[3] = {e[1] * nrm[2] - e[2] * nrm[1], e[2] * nrm[0] - e[0] * nrm[2],
                                   e[0] * nrm[1] - e[1] * nrm[0]};
@@ -539,8 +550,42 @@ __global__ void adjoint_finalize(const double* __restrict__ partial, int nchunks
                 // sum_k Re(conj r dG/dt_j) xi_c: a -> rho_i - rho_1 - rho_2, b -> rho_i + rho_1, c -> rho_i + rho_2
                 const double si = S[1 + c], s1 = S[4 + c], s2 = S[7 + c];
                 const double sj = (j == 0) ? si - s1 - s2 : (j == 1 ? si + s1 : si + s2);
-                atomicAdd(&grad[3 * v + c], S[0] * dg[c] + gam * sj);
+                const double val = S[0] * dg[c] + gam * sj;
+                out[3 * j + c] = val;
+                // |val| < 2^E with E = (biased exponent field) - 1022, also for
+                // subnormals; stored as E + 2048 > 0, so 0 means "all zero"
+                const int biased = (int)((__double_as_longlong(val) >> 52) & 0x7ff);
+                if (ok && val != 0.0) atomicMax(&expo[3 * v + c], biased - 1022 + 2048);
             }
+        }
+    }
+}
+
+// Add the corner contributions into grad in an order-independent way: each
+// contribution to (vertex v, component c) is rounded to a multiple of 2^g,
+// g = E + L - 53, where every contribution there is below 2^E in magnitude and
+// L = ceil(log2(number of corners at v)). Every partial sum is then an integer
+// times 2^g of magnitude at most 2^53 * 2^g, exact in float64, so the float64
+// atomic adds give the same bits in any order. The rounding error per
+// contribution is at most 2^(E + L - 54), the size of one float64 rounding of
+// the sum itself.
+__global__ void adjoint_scatter(const double* __restrict__ corner, const int32_t* __restrict__ tris, int64_t nt,
+                                int64_t nv, const int* __restrict__ expo, const int* __restrict__ deg,
+                                double* __restrict__ grad)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 3 * nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = tris[k];
+        if (v < 0 || v >= nv) continue;
+        const int d = deg[v];
+        const int L = 32 - __clz(d - 1);
+        for (int c = 0; c < 3; ++c) {
+            const int es = expo[3 * v + c];
+            const double val = corner[3 * k + c];
+            if (es == 0 || val == 0.0) continue;
+            const int g = es - 2048 + L - 53;
+            const double r = ldexp(rint(ldexp(val, -g)), g);
+            if (r != 0.0) atomicAdd(&grad[3 * v + c], r);
         }
     }
 }
@@ -588,9 +633,16 @@ wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n
     return WD_OK;
 }
 
+size_t wd_adjoint_scatter_bytes(int64_t nt, int64_t nv)
+{
+    const size_t corner = ((sizeof(double) * 9 * (size_t)(nt > 0 ? nt : 1)) + 255) & ~size_t(255);
+    return corner + sizeof(int) * 4 * (size_t)(nv > 0 ? nv : 1);
+}
+
 wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
                             const double* d_resid, const void* d_rec, const void* d_rec_mixed, int64_t nt,
-                            double* d_partial, const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st)
+                            double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv, double* d_grad,
+                            cudaStream_t st)
 {
     if (nt == 0) return WD_OK;
     if (plan.n_items > 0) {
@@ -604,11 +656,21 @@ wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, con
         ctx->launches++;
         WD_CUDA(cudaGetLastError());
     }
-    int64_t g = (nt + 255) / 256;
+    const size_t corner_bytes = ((sizeof(double) * 9 * (size_t)nt) + 255) & ~size_t(255);
+    double* corner = static_cast<double*>(d_scatter);
+    int* expo = reinterpret_cast<int*>(static_cast<unsigned char*>(d_scatter) + corner_bytes);
+    int* deg = expo + 3 * (nv > 0 ? nv : 1);
+    WD_CUDA(cudaMemsetAsync(expo, 0, sizeof(int) * 4 * (size_t)(nv > 0 ? nv : 1), st));
     const int64_t cap = (int64_t)ctx->num_sms * 8;
+    int64_t g = (nt + 255) / 256;
     if (g > cap) g = cap;
     adjoint_finalize<<<(int)g, 256, 0, st>>>(d_partial, plan.n_items > 0 ? plan.nchunks : 0,
-                                             static_cast<const TriRecD*>(d_rec), nt, d_tris, nv, d_grad);
+                                             static_cast<const TriRecD*>(d_rec), nt, d_tris, nv, corner, expo, deg);
+    ctx->launches++;
+    WD_CUDA(cudaGetLastError());
+    g = (3 * nt + 255) / 256;
+    if (g > cap) g = cap;
+    adjoint_scatter<<<(int)g, 256, 0, st>>>(corner, d_tris, nt, nv, expo, deg, d_grad);
     ctx->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;

@@ -415,6 +415,8 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     off += align_up(sizeof(TriRecD) * (size_t)(nt > 0 ? nt : 1));
     const size_t o_adj = off;
     off += align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) * (size_t)(nt > 0 ? nt : 1));
+    const size_t o_sc = off;
+    off += align_up(wd_adjoint_scatter_bytes(nt, nv));
     wd_status st_ = wd_ws_reserve(ctx, off);
     if (st_ != WD_OK) return st_;
     if ((st_ = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st_;
@@ -452,7 +454,8 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     void* rec64 = ctx->ws + o_rec64;
     if ((st_ = wd_launch_stage(ctx, WD_FP64, d_verts, nv, d_tris, nt, 1.0, rec64, 0, st)) != WD_OK) return st_;
     return wd_launch_adjoint(ctx, precision, ap, rule->d_xi, n, resid, rec64, precision == WD_MIXED ? rec : nullptr,
-                             nt, reinterpret_cast<double*>(ctx->ws + o_adj), d_tris, nv, d_grad, st);
+                             nt, reinterpret_cast<double*>(ctx->ws + o_adj), ctx->ws + o_sc, d_tris, nv, d_grad,
+                             st);
 }
 
 extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
@@ -508,7 +511,8 @@ extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const 
         size_t need = L.end + align_up(sizeof(double) * 2 * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1)) +
                       align_up(sizeof(TriRecD) * (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
                       align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) *
-                               (size_t)(mu->n_tris > 0 ? mu->n_tris : 1));
+                               (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
+                      align_up(wd_adjoint_scatter_bytes(mu->n_tris, mu->n_verts));
         if ((st = wd_ws_reserve(ctx, need)) != WD_OK) return st;
     }
     if ((st = upload_mesh(ctx, mu, ov, ot, strm)) != WD_OK) return st;

@@ -151,10 +151,14 @@ struct AdjPlan {
 };
 wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n_tris, AdjPlan* plan);
 // d_rec: float64 records of mu (geometry for the final scatter, and the
-// float64 adjoint); d_rec_mixed: mixed records of mu (mixed adjoint)
+// float64 adjoint); d_rec_mixed: mixed records of mu (mixed adjoint);
+// d_scatter: wd_adjoint_scatter_bytes(nt, nv) bytes of scratch. d_grad must
+// be zeroed by the caller; the result is bitwise independent of launch order.
+size_t wd_adjoint_scatter_bytes(int64_t nt, int64_t nv);
 wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
                             const double* d_resid, const void* d_rec, const void* d_rec_mixed, int64_t nt,
-                            double* d_partial, const int32_t* d_tris, int64_t nv, double* d_grad, cudaStream_t st);
+                            double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv, double* d_grad,
+                            cudaStream_t st);
 
 // batched serving kernel (wd_pair.cu), driven by a device descriptor table
 struct ServeReq {
