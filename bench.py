@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--only-n", type=int, default=None, help="restrict the sweep to one mesh (profiling runs)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-queries", type=int, default=2000)
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint batch and fitting measurement")
     return p.parse_args()
 
 
@@ -235,6 +236,66 @@ def serve_bench(wd, ctx, n_queries, rate=500.0):
             "rules": ["R=%g %dx%dx%d%s" % (r[0], r[1], r[2], r[3], " herm" if r[4] else "") for r in rules]}
 
 
+def adjoint_bench(wd, ctx):
+    """Gradient of D (s=1) w.r.t. the vertices for the batch of 64 jittered
+    meshes (sigma=0.01, seeds 0..63) at n=16 and n=32 on the 192 x 64 x 96
+    Hermitian ball rule at R=128, mixed precision, meshes resident on the
+    device; the float64 gradient of one mesh for error and speed; and the
+    200-step gradient-descent fit of the n=16, seed 0 mesh toward the sphere."""
+    import torch
+
+    from paper_2304_06340_b300.fit import fit_mesh
+    R = synth.ADJOINT_RULE
+    rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+    n_eval, _ = wd.wd_rule_info(rule)
+    res = {"rule": "R=%g %dx%dx%d herm (%d nodes evaluated)" % (R.R, R.n_r, R.n_polar, R.n_azim, n_eval),
+           "precision": "mixed", "s": 1.0, "sigma": synth.ADJOINT_SIGMA, "meshes": len(synth.ADJOINT_SEEDS)}
+    for n in synth.ADJOINT_NS:
+        dev = []
+        for sd in synth.ADJOINT_SEEDS:
+            v, t = synth.adjoint_mesh(n, sd)
+            dev.append((torch.tensor(v, device="cuda"), torch.tensor(t, device="cuda", dtype=torch.int32)))
+        out = torch.zeros(len(dev), dtype=torch.float64, device="cuda")
+        grads = [torch.zeros_like(v) for v, _ in dev]
+        for i in range(2):  # warm-up: weights cache, workspace
+            wd.wd_distance_grad_dev(ctx.handle, rule, dev[i][0], dev[i][1], None, 1.0, wd.WD_MIXED, out[i:i + 1],
+                                    grads[i])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i, (v, t) in enumerate(dev):
+            wd.wd_distance_grad_dev(ctx.handle, rule, v, t, None, 1.0, wd.WD_MIXED, out[i:i + 1], grads[i])
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        T = dev[0][1].shape[0]
+        g64 = torch.zeros_like(dev[0][0])
+        o64 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        wd.wd_distance_grad_dev(ctx.handle, rule, dev[0][0], dev[0][1], None, 1.0, wd.WD_FP64, o64, g64)
+        torch.cuda.synchronize()
+        sec64 = time.perf_counter() - t0
+        gerr = ((grads[0] - g64).norm() / g64.norm()).item()
+        res["batch_n%d" % n] = {
+            "n_tris": T, "seconds": sec, "mesh_grads_per_s": len(dev) / sec,
+            "gpairs_per_s": len(dev) * T * n_eval / sec / 1e9,
+            "pair_note": "T x nodes per mesh counted once; each is evaluated in the forward and in the adjoint",
+            "fp64_seconds_per_mesh": sec64, "speedup_vs_fp64": sec64 / (sec / len(dev)),
+            "grad_rel_err_vs_fp64": gerr, "dist_rel_err_vs_fp64": abs(out[0].item() - o64.item()) / o64.item()}
+    v, t = synth.adjoint_mesh(16, 0)
+    dv, dt = torch.tensor(v, device="cuda"), torch.tensor(t, device="cuda", dtype=torch.int32)
+    t0 = time.perf_counter()
+    r = fit_mesh(ctx, rule, dv, dt, steps=200, precision=wd.WD_MIXED)
+    sec = time.perf_counter() - t0
+    h = r.history
+    res["fit_n16"] = {"steps": r.step, "lr": r.lr, "lr_rule": "1/L, L from 8 power iterations of FD Hessian products",
+                      "D0": h[0], "D10": h[10], "D50": h[50], "D200": h[-1],
+                      "monotone": all(b <= a for a, b in zip(h, h[1:])), "seconds": sec,
+                      "radius_std_start": dv.norm(dim=1).std().item(),
+                      "radius_std_end": r.verts.norm(dim=1).std().item()}
+    return res
+
+
 def run_reference(args, cfg, queries, R):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -408,6 +469,9 @@ def main():
     serve = None
     if world == 1 and not args.no_serve and args.only_n is None:
         serve = serve_bench(wd, ctx, args.serve_queries)
+    adjoint = None
+    if world == 1 and not args.no_adjoint and args.only_n is None:
+        adjoint = adjoint_bench(wd, ctx)
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(R, queries, args.cpu_sample_seconds)
@@ -421,7 +485,7 @@ def main():
             "query_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                  "max": lat[-1], "note": "per-query kernel time, back-to-back queries"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "accuracy": accuracy, "distances": d_values[:len(dq)], "serve": serve}
+            "accuracy": accuracy, "distances": d_values[:len(dq)], "serve": serve, "adjoint": adjoint}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
