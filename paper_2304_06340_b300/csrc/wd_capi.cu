@@ -55,10 +55,11 @@ struct CoreLayout {
     size_t rec = 0, partial = 0, blockD = 0, end = 0;
 };
 
-CoreLayout core_layout(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, int64_t n_rec, size_t base)
+CoreLayout core_layout(wd_ctx* ctx, const wd_rule* rule, int precision, int mode, int64_t n_rec, size_t base)
 {
     CoreLayout L;
-    wd_plan_pair(ctx, precision, mode, n_nodes, n_rec, &L.plan);
+    const int64_t n_nodes = rule->n_eval;
+    wd_plan_pair_rule(ctx, rule, precision, mode, n_rec, &L.plan);
     size_t off = align_up(base);
     L.rec = off;
     off += align_up((size_t)n_rec * wd_tri_record_bytes(precision));
@@ -80,8 +81,7 @@ wd_status run_core(wd_ctx* ctx, wd_rule* rule, const CoreLayout& L, int precisio
     wd_status r = wd_launch_stage(ctx, precision, d_verts, nv, d_tris, nt, 1.0, rec, 0, st);
     if (r != WD_OK) return r;
     PairArgs a;
-    a.xi = rule->d_xi;
-    a.n = rule->n_eval;
+    wd_pair_args_rule(rule, a);
     a.tris = rec;
     a.T = L.plan.n_tris;
     if (mode == MODE_DIST) {
@@ -256,7 +256,7 @@ extern "C" wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule_c, const do
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     wd_rule* rule = const_cast<wd_rule*>(rule_c);
     cudaStream_t s = (cudaStream_t)stream;
-    CoreLayout L = core_layout(ctx, precision, MODE_FT, rule->n_eval, nt, 0);
+    CoreLayout L = core_layout(ctx, rule, precision, MODE_FT, nt, 0);
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     return run_core(ctx, rule, L, precision, MODE_FT, d_verts, nv, d_tris, nt, nullptr, 0.0, d_re, d_im, s);
@@ -277,7 +277,7 @@ extern "C" wd_status wd_mesh_ft(wd_ctx* ctx, const wd_rule* rule_c, const wd_mes
     size_t ov = 0, ot = align_up(sizeof(double) * 3 * mesh->n_verts);
     size_t oo = ot + align_up(sizeof(int32_t) * 3 * mesh->n_tris);
     size_t base = oo + 2 * align_up(sizeof(double) * n);
-    CoreLayout L = core_layout(ctx, precision, MODE_FT, n, mesh->n_tris, base);
+    CoreLayout L = core_layout(ctx, rule, precision, MODE_FT, mesh->n_tris, base);
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     cudaStream_t s = 0;
@@ -346,7 +346,7 @@ extern "C" wd_status wd_distance_dev(wd_ctx* ctx, const wd_rule* rule_c, const d
     if ((st = wd_activate(ctx)) != WD_OK) return st;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     wd_rule* rule = const_cast<wd_rule*>(rule_c);
-    CoreLayout L = core_layout(ctx, precision, MODE_DIST, rule->n_eval, nt + nt2, 0);
+    CoreLayout L = core_layout(ctx, rule, precision, MODE_DIST, nt + nt2, 0);
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     return run_core(ctx, rule, L, precision, MODE_DIST, d_verts, nv, d_tris, nt, nu, s, d_dist2, nullptr,
@@ -373,7 +373,7 @@ extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_me
     size_t ov2 = ot + align_up(sizeof(int32_t) * 3 * mu->n_tris);
     size_t ot2 = ov2 + (m2 ? align_up(sizeof(double) * 3 * m2->n_verts) : 0);
     size_t base = ot2 + (m2 ? align_up(sizeof(int32_t) * 3 * m2->n_tris) : 0);
-    CoreLayout L = core_layout(ctx, precision, MODE_DIST, rule->n_eval, mu->n_tris + nt2, base);
+    CoreLayout L = core_layout(ctx, rule, precision, MODE_DIST, mu->n_tris + nt2, base);
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     cudaStream_t strm = 0;
@@ -405,7 +405,7 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
 {
     const int64_t nt2 = nu->kind == WD_NU_MESH ? nu->mesh->n_tris : 0;
     const int64_t n = rule->n_eval;
-    CoreLayout L = core_layout(ctx, precision, MODE_RESID, n, nt + nt2, base);
+    CoreLayout L = core_layout(ctx, rule, precision, MODE_RESID, nt + nt2, base);
     AdjPlan ap;
     wd_plan_adjoint(ctx, precision, n, nt, &ap);
     size_t off = L.end;
@@ -427,8 +427,7 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     void* rec = ctx->ws + L.rec;
     if ((st_ = wd_launch_stage(ctx, precision, d_verts, nv, d_tris, nt, 1.0, rec, 0, st)) != WD_OK) return st_;
     PairArgs a;
-    a.xi = rule->d_xi;
-    a.n = n;
+    wd_pair_args_rule(rule, a);
     a.tris = rec;
     a.T = L.plan.n_tris;
     if (nu->kind == WD_NU_MESH) {
@@ -505,7 +504,7 @@ extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const 
     // grad_core may reallocate the scratch, so size it first with a dry layout
     {
         const int64_t nt2 = m2 ? m2->n_tris : 0;
-        CoreLayout L = core_layout(ctx, precision, MODE_RESID, rule->n_eval, mu->n_tris + nt2, base);
+        CoreLayout L = core_layout(ctx, rule, precision, MODE_RESID, mu->n_tris + nt2, base);
         AdjPlan ap;
         wd_plan_adjoint(ctx, precision, rule->n_eval, mu->n_tris, &ap);
         size_t need = L.end + align_up(sizeof(double) * 2 * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1)) +

@@ -59,8 +59,14 @@ struct wd_rule {
     int64_t n_eval = 0, n_total = 0;
     std::vector<double> h_xi;         // SoA, 3 * n_eval
     std::vector<double> h_wg;         // s-free weights
+    std::vector<double> h_rad, h_dir; // ball rules: radii and unit directions (SoA)
     double* d_xi = nullptr;           // SoA on the device
     double* d_wg = nullptr;
+    // ball rules only: node k = rad[k / n_dir] * dir[k % n_dir] (radius outer)
+    int n_rad = 0;
+    int64_t n_dir = 0;
+    double* d_rad = nullptr;          // radial nodes, n_rad
+    double* d_dir = nullptr;          // unit directions, SoA 3 * n_dir
     std::map<double, double*> w_cache;                  // s -> W_k
     std::map<std::array<double, 4>, double*> nu_cache;  // (radius, center) -> nu^ (re, im interleaved)
 };
@@ -98,6 +104,9 @@ wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double
 enum PairMode { MODE_DIST = 0, MODE_FT = 1, MODE_RESID = 2 };
 
 struct PairPlan {
+    bool radial = false;      // radius x direction node blocks (ball rules, mixed path)
+    int64_t n_dg = 0;         // radial plan: direction groups
+    int n_rg = 0;             // radial plan: radius groups
     int64_t n_nodes = 0;
     int64_t n_tris = 0;       // records (mu and, for a mesh nu, its negated triangles)
     int64_t n_nb = 0;         // node blocks
@@ -122,10 +131,16 @@ struct PairArgs {
     double* out = nullptr;        // MODE_DIST: D; MODE_FT: re[n]
     double* out_im = nullptr;     // MODE_FT: im[n]
     double* resid = nullptr;      // MODE_RESID: 2 W_k (mu^ - nu^)(xi_k), (re, im) interleaved
+    const double* rad = nullptr;  // radial plan: radii (n_rad) and unit directions (SoA, n_dir)
+    const double* dir = nullptr;
+    int n_rad = 0;
+    int64_t n_dir = 0;
 };
 
 constexpr int WD_NPB = 256;   // nodes per block: one node per thread
 constexpr int WD_TILE = 128;  // triangles per shared-memory tile
+constexpr int WD_RAD_NR = 64;                   // radial plan: radii per block (two warps per direction)
+constexpr int WD_RAD_ND = WD_NPB / WD_RAD_NR;   // radial plan: directions per block
 
 size_t wd_tri_record_bytes(int precision);
 // stage triangles (a1): records for mu (sign +1) at offset 0 and optionally a
@@ -135,6 +150,11 @@ wd_status wd_launch_stage(wd_ctx* ctx, int precision, const double* d_verts, int
                           int64_t rec_offset, cudaStream_t st);
 wd_status wd_plan_pair(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, int64_t n_tris,
                        PairPlan* plan);
+// plan for a rule: the radial kernel for ball rules in the mixed path, else as above
+wd_status wd_plan_pair_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int mode, int64_t n_tris,
+                            PairPlan* plan);
+// node arrays of a rule into the pair arguments (xi, n and, for ball rules, rad/dir)
+void wd_pair_args_rule(const wd_rule* rule, PairArgs& a);
 wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
                          const PairArgs& args, cudaStream_t st);
 wd_status wd_launch_sphere(wd_ctx* ctx, const double* d_xi, int64_t n, double radius,

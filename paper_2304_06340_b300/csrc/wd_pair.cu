@@ -192,6 +192,59 @@ __device__ __forceinline__ void pair_f64(const NodeD& q, const TriRecD& t, doubl
     fi = t.gam * gi;
 }
 
+// Largest gap >= DELTA (mixed): the divided-difference recurrence over the
+// pair with the largest gap, phases in turns about the dithered centroid
+// phase (tau, tlo); returns gamma G with gamma = gam + gam_lo.
+__device__ __forceinline__ void pair_mixed_divdiff(const TabEntry* __restrict__ tab, float tau, float tlo, float g1,
+                                                   float g2, float gam, float gam_lo, float& fr, float& fi)
+{
+    const float g3 = g2 - g1;
+    const float a1 = fabsf(g1), a2 = fabsf(g2), a3 = fabsf(g3);
+    const float ya = -(g1 + g2) * (1.0f / 3.0f);
+    const float yb = (2.0f * g1 - g2) * (1.0f / 3.0f);
+    const float yc = (2.0f * g2 - g1) * (1.0f / 3.0f);
+    const bool caseA = (a2 >= a1) && (a2 >= a3);
+    const bool caseB = !caseA && (a1 >= a3);
+    const bool caseC = !caseA && !caseB;
+    const float inv4pi = 0.0795774715459476679f;  // offsets -y/2 in turns: -y/(4 pi)
+    const float offP = caseC ? -inv4pi * yb : -inv4pi * ya;
+    const float hP = caseC ? 0.5f * g2 : 0.5f * g3;
+    const float offQ = caseB ? -inv4pi * yb : -inv4pi * yc;
+    const float hQ = caseB ? 0.5f * g2 : 0.5f * g1;
+    const float D = caseA ? g2 : (caseB ? g1 : g3);
+    float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
+    expm_turns(tab, tau + offP, tlo, cP, sP);
+    expm_turns(tab, tau + offQ, tlo, cQ, sQ);
+    const float scP = sinc32(hP), scQ = sinc32(hQ);
+    // S_P - S_Q, G = i (S_P - S_Q) / D
+    const float dr = cP * scP - cQ * scQ;
+    const float di = sP * scP - sQ * scQ;
+    const float inv = 1.0f / D;
+    const float gr = -di * inv;
+    const float gi = dr * inv;
+    // gamma carried as a float pair: its rounding is identical for congruent triangles
+    fr = fmaf(gam, gr, gam_lo * gr);
+    fi = fmaf(gam, gi, gam_lo * gi);
+}
+
+// Taylor branch, last step: gamma exp(-i t_m) (1/2 + sr + i si) with the
+// dithered phase (tau, tlo). The tail must not be added to the exactly
+// representable c/2 on its own: below half an ulp it would be rounded away
+// every time, and it has one sign (-p/24), so the loss would be a bias. It is
+// added inside the final rounding with gamma, where gamma c/2 is a full-width
+// product off the float grid.
+__device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab, float tau, float tlo, float sr,
+                                               float si, float gam, float gam_lo, float& fr, float& fi)
+{
+    float c, s;
+    expm_turns(tab, tau, tlo, c, s);  // (c, s) = exp(-i (t_m - 2 pi dith))
+    const float hc = 0.5f * c, hs = 0.5f * s;  // exact
+    const float tr = fmaf(c, sr, -s * si);
+    const float ti = fmaf(c, si, s * sr);
+    fr = fmaf(gam, hc, fmaf(gam, tr, gam_lo * (hc + tr)));
+    fi = fmaf(gam, hs, fmaf(gam, ti, gam_lo * (hs + ti)));
+}
+
 __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, const NodeF& q, const TriRecF& t,
                                            float& fr, float& fi)
 {
@@ -224,7 +277,6 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
     const float ya = -(g1 + g2) * (1.0f / 3.0f);
     const float yb = (2.0f * g1 - g2) * (1.0f / 3.0f);
     const float yc = (2.0f * g2 - g1) * (1.0f / 3.0f);
-    float gr, gi;
     if (gmax < kDelta32) {
         const float p = (g1 * g1 - g1 * g2 + g2 * g2) * (1.0f / 3.0f);
         const float qq = ya * yb * yc;
@@ -254,43 +306,10 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
         im = fmaf(im, p, 1.0f / 120.0f);
         const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
         const float si = qq * fmaf(q2, iq, im);
-        float c, s;
-        expm_turns(tab, tau, tlo, c, s);  // (c, s) = exp(-i (t_m - 2 pi dith))
-        // G = (c + i s)(1/2 + sr + i si). The tail must not be added to the
-        // exactly representable c/2 on its own: below half an ulp it would be
-        // rounded away every time, and it has one sign (-p/24), so the loss
-        // would be a bias. It is added inside the final rounding with gamma,
-        // where gamma c/2 is a full-width product off the float grid.
-        const float hc = 0.5f * c, hs = 0.5f * s;  // exact
-        const float tr = fmaf(c, sr, -s * si);
-        const float ti = fmaf(c, si, s * sr);
-        fr = fmaf(t.gam, hc, fmaf(t.gam, tr, t.gam_lo * (hc + tr)));
-        fi = fmaf(t.gam, hs, fmaf(t.gam, ti, t.gam_lo * (hs + ti)));
+        taylor_combine(tab, tau, tlo, sr, si, t.gam, t.gam_lo, fr, fi);
         return;
-    } else {
-        const bool caseA = (a2 >= a1) && (a2 >= a3);
-        const bool caseB = !caseA && (a1 >= a3);
-        const bool caseC = !caseA && !caseB;
-        const float inv4pi = 0.0795774715459476679f;  // offsets -y/2 in turns: -y/(4 pi)
-        const float offP = caseC ? -inv4pi * yb : -inv4pi * ya;
-        const float hP = caseC ? 0.5f * g2 : 0.5f * g3;
-        const float offQ = caseB ? -inv4pi * yb : -inv4pi * yc;
-        const float hQ = caseB ? 0.5f * g2 : 0.5f * g1;
-        const float D = caseA ? g2 : (caseB ? g1 : g3);
-        float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
-        expm_turns(tab, tau + offP, tlo, cP, sP);
-        expm_turns(tab, tau + offQ, tlo, cQ, sQ);
-        const float scP = sinc32(hP), scQ = sinc32(hQ);
-        // S_P - S_Q, G = i (S_P - S_Q) / D
-        const float dr = cP * scP - cQ * scQ;
-        const float di = sP * scP - sQ * scQ;
-        const float inv = 1.0f / D;
-        gr = -di * inv;
-        gi = dr * inv;
     }
-    // gamma carried as a float pair: its rounding is identical for congruent triangles
-    fr = fmaf(t.gam, gr, t.gam_lo * gr);
-    fi = fmaf(t.gam, gi, t.gam_lo * gi);
+    pair_mixed_divdiff(tab, tau, tlo, g1, g2, t.gam, t.gam_lo, fr, fi);
 }
 
 // ------------------------------------------------------------------ block reduction
@@ -309,6 +328,90 @@ __device__ __forceinline__ double block_sum(double v, double* red)
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
     return s;  // valid in warp 0
+}
+
+// Per-node end of one work item, called by every thread of the block: combine
+// the triangle chunks of the node block in fixed order (the last chunk to
+// finish does it), undo the mixed path's phase dither, then write mu^ (FT) or
+// subtract nu^, weight, write the residual (RESID) and reduce D in fixed order
+// (the last node block to finish adds the block sums).
+template <bool MIXED, int MODE>
+__device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan& p, int64_t nb, int chunk,
+                                              int64_t node, bool active, float dith, double acc_r, double acc_i,
+                                              double* red, int& s_last)
+{
+    const int64_t n = a.n;
+    // ---- combine triangle chunks of this node block (fixed order)
+    double mr = acc_r, mi = acc_i;
+    if (p.nchunks > 1) {
+        if (active) {
+            a.partial[2 * ((int64_t)chunk * n + node)] = acc_r;
+            a.partial[2 * ((int64_t)chunk * n + node) + 1] = acc_i;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(&a.cnt[nb], 1) == p.nchunks - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        mr = 0.0;
+        mi = 0.0;
+        if (active)
+            for (int c = 0; c < p.nchunks; ++c) {
+                mr += __ldcg(&a.partial[2 * ((int64_t)c * n + node)]);
+                mi += __ldcg(&a.partial[2 * ((int64_t)c * n + node) + 1]);
+            }
+        if (threadIdx.x == 0) a.cnt[nb] = 0;  // ready for the next launch
+    }
+
+    if (MIXED) {
+        // undo the phase dither: mu^ = S exp(-2 pi i dith), in float64
+        double sd, cd;
+        sincospi(2.0 * (double)dith, &sd, &cd);
+        const double r_ = mr * cd + mi * sd;
+        mi = mi * cd - mr * sd;
+        mr = r_;
+    }
+
+    if (MODE == MODE_FT) {
+        if (active) {
+            a.out[node] = mr;
+            a.out_im[node] = mi;
+        }
+        return;
+    }
+
+    // ---- distance epilogue (a6, a7): subtract nu^, weight, reduce
+    double term = 0.0;
+    if (active) {
+        double dr = mr, di = mi;
+        if (a.nu) {
+            dr -= a.nu[2 * node];
+            di -= a.nu[2 * node + 1];
+        }
+        term = a.W[node] * (dr * dr + di * di);
+        if (MODE == MODE_RESID) {
+            a.resid[2 * node] = 2.0 * a.W[node] * dr;
+            a.resid[2 * node + 1] = 2.0 * a.W[node] * di;
+        }
+    }
+    const double bsum = block_sum(term, red);
+    if (threadIdx.x == 0) {
+        a.blockD[nb] = bsum;
+        __threadfence();
+        s_last = (atomicAdd(a.done, 1) == (int)(p.n_nb - 1));
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        double v = 0.0;
+        for (int64_t i = threadIdx.x; i < p.n_nb; i += WD_NPB) v += __ldcg(&a.blockD[i]);
+        const double tot = block_sum(v, red);
+        if (threadIdx.x == 0) {
+            a.out[0] = tot;
+            *a.done = 0;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ pair kernel (a3..a7)
@@ -395,77 +498,163 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
             }
         }
 
-        // ---- combine triangle chunks of this node block (fixed order)
-        double mr = acc_r, mi = acc_i;
-        if (p.nchunks > 1) {
-            if (active) {
-                a.partial[2 * ((int64_t)chunk * n + node)] = acc_r;
-                a.partial[2 * ((int64_t)chunk * n + node) + 1] = acc_i;
-            }
-            __threadfence();
+        node_epilogue<MIXED, MODE>(a, p, nb, chunk, node, active, MIXED ? qf.dith : 0.0f, acc_r, acc_i, red,
+                                   s_last);
+    }
+}
+
+// ------------------------------------------------------------------ radial pair kernel (mixed, ball rules)
+// Ball-rule nodes factor as xi = r omega (radius r, unit direction omega), so
+// every per-pair quantity that is linear in xi is a per-(direction, triangle)
+// rate times r: the centroid phase t_m = r (omega.m), the gaps g1 = r (omega.e1),
+// g2 = r (omega.e2). In the Taylor branch p = r^2 p0 and q = r^3 q0, so the
+// tail Psi - 1/2 = sr + i si is a polynomial in rho = r^2:
+//     sr = rho (R1 + rho (R2 + ... + rho R6)),  si = r^3 (I0 + rho (I1 + ... + rho I4)),
+// the same terms (h_n to n = 12) as the per-node kernel, regrouped by powers of
+// r. A block covers WD_RAD_ND directions x WD_RAD_NR radii; for each tile of
+// triangles it first computes one record of rates and coefficients per
+// (direction, triangle), in float64 for the phase rate, then every thread runs
+// over the tile with its own radius. A warp holds 32 radii of one direction,
+// so the record loads are broadcasts.
+struct __align__(16) RadRec {
+    float dmh, dml;      // omega.m / 2 pi in turns per unit radius, float pair
+    float gmax0;         // largest |gap| per unit radius
+    float gam;           // gamma, high part (0 for padding)
+    float gam_lo;
+    float R[6];          // real tail coefficients R1..R6
+    float I[5];          // imaginary tail coefficients I0..I4
+    float d1, d2;        // omega.e1, omega.e2
+    float pad[2];
+};
+static_assert(sizeof(RadRec) == 80, "RadRec layout");
+
+__device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __restrict__ dir, int64_t n_dir,
+                                            int64_t d, RadRec& o)
+{
+    const double inv2pi = 0.15915494309189533576888376337251;
+    const double wx = dir[d], wy = dir[n_dir + d], wz = dir[2 * n_dir + d];
+    // centroid (mh + ml is exact in float64)
+    const double mx = (double)t.mh[0] + (double)t.ml[0];
+    const double my = (double)t.mh[1] + (double)t.ml[1];
+    const double mz = (double)t.mh[2] + (double)t.ml[2];
+    const double dm = fma(wx, mx, fma(wy, my, wz * mz)) * inv2pi;
+    o.dmh = (float)dm;
+    o.dml = (float)(dm - (double)o.dmh);
+    const float fx = (float)wx, fy = (float)wy, fz = (float)wz;
+    const float d1 = fmaf(fx, t.e1[0], fmaf(fy, t.e1[1], fz * t.e1[2]));
+    const float d2 = fmaf(fx, t.e2[0], fmaf(fy, t.e2[1], fz * t.e2[2]));
+    o.d1 = d1;
+    o.d2 = d2;
+    o.gmax0 = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d2 - d1)));
+    o.gam = t.gam;
+    o.gam_lo = t.gam_lo;
+    const float ya = -(d1 + d2) * (1.0f / 3.0f);
+    const float yb = (2.0f * d1 - d2) * (1.0f / 3.0f);
+    const float yc = (2.0f * d2 - d1) * (1.0f / 3.0f);
+    const float p0 = (d1 * d1 - d1 * d2 + d2 * d2) * (1.0f / 3.0f);
+    const float A0 = fmaf(d1, d1 - d2, d2 * d2);  // 3 p0
+    const float q0 = ya * yb * yc;
+    const float q02 = q0 * q0;
+    const float p2 = p0 * p0, p3 = p2 * p0, p4 = p2 * p2;
+    // -A0/72 with 1/72 as a float pair (a rounded 1/72 would bias every triangle alike)
+    o.R[0] = fmaf(A0, -1.388888899e-02f, A0 * 1.034802868e-10f);
+    o.R[1] = p2 * (1.0f / 720.0f);
+    o.R[2] = -(p3 + q02) * (1.0f / 40320.0f);
+    o.R[3] = fmaf(3.0f * q02, p0, p4) * (1.0f / 3628800.0f);
+    o.R[4] = -fmaf(6.0f * q02, p2, p4 * p0) * (1.0f / 479001600.0f);
+    o.R[5] = fmaf(10.0f * q02, p3, fmaf(p3, p3, q02 * q02)) * (1.0f / 87178291200.0f);
+    o.I[0] = q0 * (1.0f / 120.0f);
+    o.I[1] = -2.0f * q0 * p0 * (1.0f / 5040.0f);
+    o.I[2] = 3.0f * q0 * p2 * (1.0f / 362880.0f);
+    o.I[3] = -q0 * fmaf(4.0f, p3, q02) * (1.0f / 39916800.0f);
+    o.I[4] = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
+    o.pad[0] = o.pad[1] = 0.0f;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a, const PairPlan p)
+{
+    __shared__ __align__(16) RadRec tile[WD_RAD_ND][WD_TILE];
+    __shared__ double red[WD_NPB / 32];
+    __shared__ int s_last;
+    __shared__ TabEntry etab[kTab];
+    fill_exp_table(etab);  // visible after the first tile barrier
+
+    const int dl = threadIdx.x / WD_RAD_NR;  // direction within the block (warp-uniform)
+    const int rl = threadIdx.x % WD_RAD_NR;
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const int64_t nb = item / p.nchunks;
+        const int chunk = (int)(item - nb * p.nchunks);
+        const int64_t dg = nb / p.n_rg;
+        const int rg = (int)(nb - dg * p.n_rg);
+        const int64_t d = dg * WD_RAD_ND + dl;
+        const int ir = rg * WD_RAD_NR + rl;
+        const bool dir_ok = d < a.n_dir;
+        const bool active = dir_ok && ir < a.n_rad;
+        const int64_t node = active ? (int64_t)ir * a.n_dir + d : 0;
+        // this thread's radius: float pair, r^2, r^3, and the Taylor bound on gmax0
+        const double r = active ? a.rad[ir] : 0.0;
+        const float rh = (float)r, rlo = (float)(r - (double)rh);
+        const float rho = (float)(r * r), r3 = (float)(r * r * r);
+        const float thr = active ? (float)((double)kDelta32 / r) : 3.402823466e38f;
+        const float dith = node_dither(node);
+
+        const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
+        int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
+        if (t1 > a.T) t1 = a.T;
+        double acc_r = 0.0, acc_i = 0.0;
+        for (int64_t tb = t0; tb < t1; tb += WD_TILE) {
+            const int cnt = (int)((t1 - tb) < WD_TILE ? (t1 - tb) : WD_TILE);
+            const int cnt4 = (cnt + 3) & ~3;
             __syncthreads();
-            if (threadIdx.x == 0) s_last = (atomicAdd(&a.cnt[nb], 1) == p.nchunks - 1);
-            __syncthreads();
-            if (!s_last) continue;
-            __threadfence();
-            mr = 0.0;
-            mi = 0.0;
-            if (active)
-                for (int c = 0; c < p.nchunks; ++c) {
-                    mr += __ldcg(&a.partial[2 * ((int64_t)c * n + node)]);
-                    mi += __ldcg(&a.partial[2 * ((int64_t)c * n + node) + 1]);
+            // records for WD_RAD_ND directions x cnt4 triangles (zero padding: gamma = 0)
+            for (int i = threadIdx.x; i < WD_RAD_ND * WD_TILE; i += WD_NPB) {
+                const int di = i / WD_TILE, j = i % WD_TILE;
+                const int64_t dd = dg * WD_RAD_ND + di;
+                if (j >= cnt4) continue;
+                RadRec o;
+                if (j < cnt && dd < a.n_dir) {
+                    const TriRecF tr = static_cast<const TriRecF*>(a.tris)[tb + j];
+                    make_radrec(tr, a.dir, a.n_dir, dd, o);
+                } else {
+                    o = RadRec{};
                 }
-            if (threadIdx.x == 0) a.cnt[nb] = 0;  // ready for the next launch
-        }
-
-        if (MIXED) {
-            // undo the phase dither: mu^ = S exp(-2 pi i dith), in float64
-            double sd, cd;
-            sincospi(2.0 * (double)qf.dith, &sd, &cd);
-            const double r_ = mr * cd + mi * sd;
-            mi = mi * cd - mr * sd;
-            mr = r_;
-        }
-
-        if (MODE == MODE_FT) {
-            if (active) {
-                a.out[node] = mr;
-                a.out_im[node] = mi;
+                tile[di][j] = o;
             }
-            continue;
-        }
-
-        // ---- distance epilogue (a6, a7): subtract nu^, weight, reduce
-        double term = 0.0;
-        if (active) {
-            double dr = mr, di = mi;
-            if (a.nu) {
-                dr -= a.nu[2 * node];
-                di -= a.nu[2 * node + 1];
+            __syncthreads();
+            if (!dir_ok) continue;  // warp-uniform
+            const RadRec* rec = tile[dl];
+            Kahan kr, ki;
+            for (int j = 0; j < cnt4; j += 4) {
+                float br = 0.0f, bi = 0.0f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const RadRec& t = rec[j + jj];
+                    // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
+                    const float P = rh * t.dmh;
+                    const float e = fmaf(rh, t.dmh, -P);
+                    const float lo = fmaf(rh, t.dml, fmaf(rlo, t.dmh, e));
+                    const float tau = (P - rintf(P)) - dith;
+                    float fr, fi;
+                    if (t.gmax0 < thr) {
+                        float sr = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
+                        sr = fmaf(sr, rho, t.R[0]) * rho;
+                        float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
+                        si = fmaf(si, rho, t.I[0]) * r3;
+                        taylor_combine(etab, tau, lo, sr, si, t.gam, t.gam_lo, fr, fi);
+                    } else {
+                        pair_mixed_divdiff(etab, tau, lo, rh * t.d1, rh * t.d2, t.gam, t.gam_lo, fr, fi);
+                    }
+                    br += fr;
+                    bi += fi;
+                }
+                kr.add(br);
+                ki.add(bi);
             }
-            term = a.W[node] * (dr * dr + di * di);
-            if (MODE == MODE_RESID) {
-                a.resid[2 * node] = 2.0 * a.W[node] * dr;
-                a.resid[2 * node + 1] = 2.0 * a.W[node] * di;
-            }
+            acc_r += kr.value();
+            acc_i += ki.value();
         }
-        const double bsum = block_sum(term, red);
-        if (threadIdx.x == 0) {
-            a.blockD[nb] = bsum;
-            __threadfence();
-            s_last = (atomicAdd(a.done, 1) == (int)(p.n_nb - 1));
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            double v = 0.0;
-            for (int64_t i = threadIdx.x; i < p.n_nb; i += WD_NPB) v += __ldcg(&a.blockD[i]);
-            const double tot = block_sum(v, red);
-            if (threadIdx.x == 0) {
-                a.out[0] = tot;
-                *a.done = 0;
-            }
-        }
+        node_epilogue<true, MODE>(a, p, nb, chunk, node, active, dith, acc_r, acc_i, red, s_last);
     }
 }
 
@@ -485,6 +674,51 @@ int resident_blocks(wd_ctx* ctx)
         c = per_sm * ctx->num_sms;
     }
     return c;
+}
+
+template <int MODE>
+int resident_radial(wd_ctx* ctx)
+{
+    static int cached[64] = {0};
+    int& c = cached[ctx->device & 63];
+    if (c == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel_radial<MODE>, WD_NPB, 0) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        c = per_sm * ctx->num_sms;
+    }
+    return c;
+}
+
+int resident_radial_for(wd_ctx* ctx, int mode)
+{
+    if (mode == MODE_FT) return resident_radial<MODE_FT>(ctx);
+    if (mode == MODE_RESID) return resident_radial<MODE_RESID>(ctx);
+    return resident_radial<MODE_DIST>(ctx);
+}
+
+// Split the triangle range into chunks only when the node blocks alone cannot
+// fill the GPU (about four waves of resident blocks).
+void plan_chunks(PairPlan& p, int64_t resident)
+{
+    p.n_tiles = (p.n_tris + WD_TILE - 1) / WD_TILE;
+    const int64_t target = 4 * resident;
+    int64_t nchunks = 1;
+    if (p.n_nb > 0 && p.n_nb < target && p.n_tiles > 1) {
+        nchunks = (target + p.n_nb - 1) / p.n_nb;
+        if (nchunks > p.n_tiles) nchunks = p.n_tiles;
+    }
+    int64_t tpc = p.n_tiles > 0 ? (p.n_tiles + nchunks - 1) / nchunks : 0;
+    if (tpc > 0) nchunks = (p.n_tiles + tpc - 1) / tpc;
+    if (nchunks < 1) nchunks = 1;
+    p.tiles_per_chunk = (int)tpc;
+    p.nchunks = (int)nchunks;
+    p.n_items = p.n_nb * p.nchunks;
+    p.grid = (int)(p.n_items < resident ? p.n_items : resident);
 }
 
 int resident_for(wd_ctx* ctx, int precision, int mode)
@@ -649,31 +883,51 @@ wd_status wd_plan_pair(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, in
     p.n_nodes = n_nodes;
     p.n_tris = n_tris;
     p.n_nb = (n_nodes + WD_NPB - 1) / WD_NPB;
-    p.n_tiles = (n_tris + WD_TILE - 1) / WD_TILE;
-    const int64_t resident = resident_for(ctx, precision, mode);
-    // split the triangle range only when node blocks alone cannot fill the GPU
-    const int64_t target = 4 * resident;
-    int64_t nchunks = 1;
-    if (p.n_nb > 0 && p.n_nb < target && p.n_tiles > 1) {
-        nchunks = (target + p.n_nb - 1) / p.n_nb;
-        if (nchunks > p.n_tiles) nchunks = p.n_tiles;
-    }
-    int64_t tpc = p.n_tiles > 0 ? (p.n_tiles + nchunks - 1) / nchunks : 0;
-    if (tpc > 0) nchunks = (p.n_tiles + tpc - 1) / tpc;
-    if (nchunks < 1) nchunks = 1;
-    p.tiles_per_chunk = (int)tpc;
-    p.nchunks = (int)nchunks;
-    p.n_items = p.n_nb * p.nchunks;
-    p.grid = (int)(p.n_items < resident ? p.n_items : resident);
+    plan_chunks(p, resident_for(ctx, precision, mode));
     *plan = p;
     return WD_OK;
+}
+
+wd_status wd_plan_pair_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int mode, int64_t n_tris,
+                            PairPlan* plan)
+{
+    if (precision != WD_MIXED || !rule->d_rad || rule->n_dir <= 0)
+        return wd_plan_pair(ctx, precision, mode, rule->n_eval, n_tris, plan);
+    PairPlan p;
+    p.radial = true;
+    p.n_nodes = rule->n_eval;
+    p.n_tris = n_tris;
+    p.n_dg = (rule->n_dir + WD_RAD_ND - 1) / WD_RAD_ND;
+    p.n_rg = (rule->n_rad + WD_RAD_NR - 1) / WD_RAD_NR;
+    p.n_nb = p.n_dg * p.n_rg;
+    plan_chunks(p, resident_radial_for(ctx, mode));
+    *plan = p;
+    return WD_OK;
+}
+
+void wd_pair_args_rule(const wd_rule* rule, PairArgs& a)
+{
+    a.xi = rule->d_xi;
+    a.n = rule->n_eval;
+    a.rad = rule->d_rad;
+    a.dir = rule->d_dir;
+    a.n_rad = rule->n_rad;
+    a.n_dir = rule->n_dir;
 }
 
 wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
                          const PairArgs& args, cudaStream_t st)
 {
     if (plan.n_items == 0) return WD_OK;
-    if (precision == WD_MIXED) {
+    if (plan.radial) {
+        if (precision != WD_MIXED || !args.rad || !args.dir) {
+            wd_set_error("internal: radial plan without a mixed ball rule");
+            return WD_EINVAL;
+        }
+        if (mode == MODE_FT) pair_kernel_radial<MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        else if (mode == MODE_RESID) pair_kernel_radial<MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        else pair_kernel_radial<MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+    } else if (precision == WD_MIXED) {
         if (mode == MODE_FT) pair_kernel<true, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else if (mode == MODE_RESID) pair_kernel<true, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else pair_kernel<true, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);

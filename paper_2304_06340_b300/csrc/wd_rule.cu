@@ -108,6 +108,12 @@ wd_status upload_rule(wd_ctx* ctx, wd_rule* r)
         WD_CUDA(cudaMemcpy(r->d_xi, r->h_xi.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
         WD_CUDA(cudaMemcpy(r->d_wg, r->h_wg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     }
+    if (!r->h_rad.empty()) {
+        WD_CUDA(cudaMalloc(&r->d_rad, sizeof(double) * r->h_rad.size()));
+        WD_CUDA(cudaMalloc(&r->d_dir, sizeof(double) * r->h_dir.size()));
+        WD_CUDA(cudaMemcpy(r->d_rad, r->h_rad.data(), sizeof(double) * r->h_rad.size(), cudaMemcpyHostToDevice));
+        WD_CUDA(cudaMemcpy(r->d_dir, r->h_dir.data(), sizeof(double) * r->h_dir.size(), cudaMemcpyHostToDevice));
+    }
     r->ctx = ctx;
     return WD_OK;
 }
@@ -117,6 +123,8 @@ void release_rule(wd_rule* r)
     if (!r) return;
     cudaFree(r->d_xi);
     cudaFree(r->d_wg);
+    cudaFree(r->d_rad);
+    cudaFree(r->d_dir);
     for (auto& kv : r->w_cache) cudaFree(kv.second);
     for (auto& kv : r->nu_cache) cudaFree(kv.second);
     delete r;
@@ -257,6 +265,20 @@ extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_r
     }
     const long double w_phi = 2.0L * kPi / d->n_azim;
     const long double half_R = 0.5L * (long double)d->R;
+    // the same nodes factored as radius x unit direction, for the radial kernel
+    r->n_rad = d->n_r;
+    r->n_dir = (int64_t)n_u * d->n_azim;
+    r->h_rad.resize(d->n_r);
+    r->h_dir.resize(3 * r->n_dir);
+    for (int i = 0; i < d->n_r; ++i) r->h_rad[i] = (double)(half_R * (1.0L + xr[i]));
+    for (int j = 0, kd = 0; j < n_u; ++j) {
+        const long double u = xu[u0 + j], sn = sqrtl(1.0L - u * u);
+        for (int m = 0; m < d->n_azim; ++m, ++kd) {
+            r->h_dir[kd] = (double)(sn * cph[m]);
+            r->h_dir[r->n_dir + kd] = (double)(sn * sph[m]);
+            r->h_dir[2 * r->n_dir + kd] = (double)u;
+        }
+    }
     int64_t k = 0;
     for (int i = 0; i < d->n_r; ++i) {
         long double rr = half_R * (1.0L + xr[i]);
