@@ -307,8 +307,9 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __
                                                                 const AdjPlan p, double* __restrict__ partial)
 {
     __shared__ AdjNodeF sn[ADJ_NPT];
-    __shared__ TabEntry etab[kTab];
+    __shared__ TabEntry etab[kTab * kTabRep];
     fill_exp_table(etab);
+    const TabEntry* tl = exp_table_lane(etab);
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
         const int64_t tb = item / p.nchunks;
         const int chunk = (int)(item - tb * p.nchunks);
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __
                     const float P1r = fmaf(Ppr, yb, Pqr * dq1), P1i = fmaf(Ppi, yb, Pqi * dq1);
                     const float P2r = fmaf(Ppr, yc, Pqr * dq2), P2i = fmaf(Ppi, yc, Pqi * dq2);
                     float c, s;
-                    expm_turns(etab, tau, lo, c, s);  // exp(-i (t_m - 2 pi d)) = (c, s)
+                    expm_turns(tl, tau, lo, c, s);  // exp(-i (t_m - 2 pi d)) = (c, s)
                     // Z = conj(r') E
                     const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
                     rho0h = Zr;
@@ -453,8 +454,8 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __
                     const float offQ = oQ1 * g1 + oQ2 * g2, hQ = hQ1 * g1 + hQ2 * g2;
                     const float inv2pif = 0.159154943091895336f;
                     float cP, sP, cQ, sQ;
-                    expm_turns(etab, tau + offP * inv2pif, lo, cP, sP);
-                    expm_turns(etab, tau + offQ * inv2pif, lo, cQ, sQ);
+                    expm_turns(tl, tau + offP * inv2pif, lo, cP, sP);
+                    expm_turns(tl, tau + offQ * inv2pif, lo, cQ, sQ);
                     float scP, dscP, scQ, dscQ;
                     sincd32(hP, scP, dscP);
                     sincd32(hQ, scQ, dscQ);

@@ -141,6 +141,7 @@ constexpr int WD_NPB = 256;   // nodes per block: one node per thread
 constexpr int WD_TILE = 128;  // triangles per shared-memory tile
 constexpr int WD_RAD_NR = 64;                   // radial plan: radii per block (two warps per direction)
 constexpr int WD_RAD_ND = WD_NPB / WD_RAD_NR;   // radial plan: directions per block
+constexpr int WD_RAD_TILE = 64;                 // radial plan: triangles per record tile
 
 size_t wd_tri_record_bytes(int precision);
 // stage triangles (a1): records for mu (sign +1) at offset 0 and optionally a

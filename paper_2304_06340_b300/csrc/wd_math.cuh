@@ -60,20 +60,29 @@ __device__ __forceinline__ float sinc32(float x)
 }
 
 // exp(-i 2 pi tau) for a phase in turns given as the unevaluated float pair
-// tau + tlo, without rounding 2 pi into the argument. tau = j/256 + u with j
+// tau + tlo, without rounding 2 pi into the argument. tau = j/128 + u with j
 // the nearest multiple (found with a magic-number add, so no float-to-int
-// conversion) and |u| <= 1/512 exactly; exp(-2 pi i j/256) comes from a table
+// conversion) and |u| <= 1/256 exactly; exp(-2 pi i j/128) comes from a table
 // of float pairs (hi + lo, from float64 sincospi), exp(-i x), x = 2 pi u, from
-// short Taylor polynomials (|x| <= pi/256: remainders below 3e-12), and the
-// two are combined in pair arithmetic. Unlike a float32 polynomial on a quarter
-// turn, whose rounded coefficients bias its mean amplitude by about 1e-9,
-// this has a mean relative bias near 1e-11, which matters because the phases
-// of a node's triangles are uniformly spread and any mean bias scales mu^.
-constexpr int kTab = 256;
+// short Taylor polynomials (|x| <= pi/128: cos remainder 3e-13; the sin
+// remainder, 7e-11, is odd in x and moves the mean amplitude by 5e-13), and
+// the two are combined in pair arithmetic. Unlike a float32 polynomial on a
+// quarter turn, whose rounded coefficients bias its mean amplitude by about
+// 1e-9, this has a mean relative bias near 1e-11, which matters because the
+// phases of a node's triangles are uniformly spread and any mean bias scales
+// mu^.
+//
+// The table lives in shared memory as kTabRep interleaved replicas (entry j
+// of replica c at j * kTabRep + c) and lane l reads replica l mod kTabRep: the
+// eight lanes served together by a 128-bit shared load then always fall in
+// different bank groups, whatever their (data-dependent) entries.
+constexpr int kTab = 128;
+constexpr int kTabRep = 8;
 struct __align__(16) TabEntry {
-    float ch, cl, sh, sl;  // cos and sin of 2 pi j / 256 as float pairs
+    float ch, cl, sh, sl;  // cos and sin of 2 pi j / 128 as float pairs
 };
 
+// fills kTab * kTabRep entries; visible after the caller's next barrier
 __device__ __forceinline__ void fill_exp_table(TabEntry* tab)
 {
     for (int j = threadIdx.x; j < kTab; j += blockDim.x) {
@@ -84,18 +93,25 @@ __device__ __forceinline__ void fill_exp_table(TabEntry* tab)
         e.cl = (float)(cd - (double)e.ch);
         e.sh = (float)sd;
         e.sl = (float)(sd - (double)e.sh);
-        tab[j] = e;
+#pragma unroll
+        for (int c = 0; c < kTabRep; ++c) tab[j * kTabRep + c] = e;
     }
 }
 
-__device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tab, float tau, float tlo,
+// this thread's replica of the table
+__device__ __forceinline__ const TabEntry* exp_table_lane(const TabEntry* tab)
+{
+    return tab + (threadIdx.x & (kTabRep - 1));
+}
+
+__device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, float tau, float tlo,
                                            float& er, float& ei)
 {
     const float magic = 12582912.0f;  // 1.5 * 2^23: rounds to an integer in the low bits
     const float km = fmaf(tau, (float)kTab, magic);
     const int idx = __float_as_int(km) & (kTab - 1);
     const float k = km - magic;                   // exact
-    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/512
+    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/256
     const float xh = u * 6.28318548202514648f;
     float xl = fmaf(u, 6.28318548202514648f, -xh);
     xl = fmaf(u, -1.74845553e-7f, xl);            // 2 pi - float(2 pi)
@@ -104,10 +120,12 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tab, flo
     // cos x - 1 and sin x - xh
     const float dc = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), -xh * xl);
     const float ds = fmaf(xh * x2, -1.0f / 6.0f, xl);
-    const TabEntry t = tab[idx];
-    // cos(theta) = Tc (1 + dc) - Ts sin x, sin(theta) = Ts (1 + dc) + Tc sin x
-    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, xh, t.cl + fmaf(-t.sh, ds, -t.sl * xh)));
-    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, xh, t.sl + fmaf(t.ch, ds, t.cl * xh)));
+    const TabEntry t = tl[idx * kTabRep];
+    // cos(theta) = Tc (1 + dc) - Ts sin x, sin(theta) = Ts (1 + dc) + Tc sin x,
+    // with the table's low parts applied to the leading 1 only: their products
+    // with x (below 1e-9, zero mean over the phases) are left out
+    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, xh, fmaf(-t.sh, ds, t.cl)));
+    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, xh, fmaf(t.ch, ds, t.sl)));
     er = c;   // exp(-i theta) = cos theta - i sin theta
     ei = -s;
 }

@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
     __shared__ __align__(16) Rec tile[WD_TILE];
     __shared__ double red[WD_NPB / 32];
     __shared__ int s_last;
-    __shared__ TabEntry etab[kTab];
+    __shared__ TabEntry etab[kTab * kTabRep];
     if (MIXED) fill_exp_table(etab);  // visible after the first tile barrier
 
     const int64_t n = a.n;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         float fr, fi;
-                        pair_mixed(etab, qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
+                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
                         br += fr;
                         bi += fi;
                     }
@@ -519,10 +519,10 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
 struct __align__(16) RadRec {
     float dmh, dml;      // omega.m / 2 pi in turns per unit radius, float pair
     float gmax0;         // largest |gap| per unit radius
-    float gam;           // gamma, high part (0 for padding)
-    float gam_lo;
-    float R[6];          // real tail coefficients R1..R6
-    float I[5];          // imaginary tail coefficients I0..I4
+    float g2;            // gamma / 2, high part (0 for padding)
+    float l2;            // gamma / 2, low part
+    float R[6];          // real tail coefficients R1..R6, times 2
+    float I[5];          // imaginary tail coefficients I0..I4, times 2
     float d1, d2;        // omega.e1, omega.e2
     float pad[2];
 };
@@ -546,8 +546,8 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __re
     o.d1 = d1;
     o.d2 = d2;
     o.gmax0 = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d2 - d1)));
-    o.gam = t.gam;
-    o.gam_lo = t.gam_lo;
+    o.g2 = 0.5f * t.gam;  // exact
+    o.l2 = 0.5f * t.gam_lo;
     const float ya = -(d1 + d2) * (1.0f / 3.0f);
     const float yb = (2.0f * d1 - d2) * (1.0f / 3.0f);
     const float yc = (2.0f * d2 - d1) * (1.0f / 3.0f);
@@ -568,17 +568,38 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __re
     o.I[2] = 3.0f * q0 * p2 * (1.0f / 362880.0f);
     o.I[3] = -q0 * fmaf(4.0f, p3, q02) * (1.0f / 39916800.0f);
     o.I[4] = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
+    for (int k = 0; k < 6; ++k) o.R[k] *= 2.0f;  // exact
+    for (int k = 0; k < 5; ++k) o.I[k] *= 2.0f;
     o.pad[0] = o.pad[1] = 0.0f;
+}
+
+// Taylor branch end for the radial kernel, with the doubled tail 2 (sr + i si)
+// and g2 = gamma/2, l2 = gamma_lo/2:
+//     F = gamma (c + i s)(1/2 + sr + i si)
+//       = (gamma/2)(c + i s) + (gamma/2)(c + i s)(2 sr + 2 i si) + (gamma_lo/2)(c + i s),
+// gamma/2 and gamma_lo/2 exact, all in one final rounding per component as in
+// taylor_combine. The product gamma_lo * tail (2^-24 of a zero-mean term
+// already below the float32 rounding of F) is left out.
+__device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__ tl, float tau, float tlo,
+                                                    float sr2, float si2, float g2, float l2, float& fr, float& fi)
+{
+    float c, s;
+    expm_turns(tl, tau, tlo, c, s);
+    const float tr = fmaf(c, sr2, -s * si2);
+    const float ti = fmaf(c, si2, s * sr2);
+    fr = fmaf(g2, c, fmaf(g2, tr, l2 * c));
+    fi = fmaf(g2, s, fmaf(g2, ti, l2 * s));
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a, const PairPlan p)
 {
-    __shared__ __align__(16) RadRec tile[WD_RAD_ND][WD_TILE];
+    __shared__ __align__(16) RadRec tile[WD_RAD_ND][WD_RAD_TILE];
     __shared__ double red[WD_NPB / 32];
     __shared__ int s_last;
-    __shared__ TabEntry etab[kTab];
+    __shared__ TabEntry etab[kTab * kTabRep];
     fill_exp_table(etab);  // visible after the first tile barrier
+    const TabEntry* tl = exp_table_lane(etab);
 
     const int dl = threadIdx.x / WD_RAD_NR;  // direction within the block (warp-uniform)
     const int rl = threadIdx.x % WD_RAD_NR;
@@ -603,15 +624,15 @@ __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a
         int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
         if (t1 > a.T) t1 = a.T;
         double acc_r = 0.0, acc_i = 0.0;
-        for (int64_t tb = t0; tb < t1; tb += WD_TILE) {
-            const int cnt = (int)((t1 - tb) < WD_TILE ? (t1 - tb) : WD_TILE);
-            const int cnt4 = (cnt + 3) & ~3;
+        for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
+            const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
+            const int cnt8 = (cnt + 7) & ~7;
             __syncthreads();
-            // records for WD_RAD_ND directions x cnt4 triangles (zero padding: gamma = 0)
-            for (int i = threadIdx.x; i < WD_RAD_ND * WD_TILE; i += WD_NPB) {
-                const int di = i / WD_TILE, j = i % WD_TILE;
+            // records for WD_RAD_ND directions x cnt8 triangles (zero padding: gamma = 0)
+            for (int i = threadIdx.x; i < WD_RAD_ND * WD_RAD_TILE; i += WD_NPB) {
+                const int di = i / WD_RAD_TILE, j = i % WD_RAD_TILE;
                 const int64_t dd = dg * WD_RAD_ND + di;
-                if (j >= cnt4) continue;
+                if (j >= cnt8) continue;
                 RadRec o;
                 if (j < cnt && dd < a.n_dir) {
                     const TriRecF tr = static_cast<const TriRecF*>(a.tris)[tb + j];
@@ -624,11 +645,13 @@ __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a
             __syncthreads();
             if (!dir_ok) continue;  // warp-uniform
             const RadRec* rec = tile[dl];
+            // plain float32 sums over groups of 8 pairs (dithered phases: random
+            // roundings), Kahan across groups
             Kahan kr, ki;
-            for (int j = 0; j < cnt4; j += 4) {
+            for (int j = 0; j < cnt8; j += 8) {
                 float br = 0.0f, bi = 0.0f;
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
+                for (int jj = 0; jj < 8; ++jj) {
                     const RadRec& t = rec[j + jj];
                     // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
                     const float P = rh * t.dmh;
@@ -641,9 +664,9 @@ __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a
                         sr = fmaf(sr, rho, t.R[0]) * rho;
                         float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
                         si = fmaf(si, rho, t.I[0]) * r3;
-                        taylor_combine(etab, tau, lo, sr, si, t.gam, t.gam_lo, fr, fi);
+                        taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi);
                     } else {
-                        pair_mixed_divdiff(etab, tau, lo, rh * t.d1, rh * t.d2, t.gam, t.gam_lo, fr, fi);
+                        pair_mixed_divdiff(tl, tau, lo, rh * t.d1, rh * t.d2, 2.0f * t.g2, 2.0f * t.l2, fr, fi);
                     }
                     br += fr;
                     bi += fi;
@@ -748,7 +771,7 @@ __global__ void __launch_bounds__(WD_NPB) serve_kernel(const ServeTable* __restr
     using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
     __shared__ __align__(16) Rec tile[WD_TILE];
     __shared__ double red[WD_NPB / 32];
-    __shared__ TabEntry etab[kTab];
+    __shared__ TabEntry etab[kTab * kTabRep];
     if (MIXED) fill_exp_table(etab);
     const int n_items = head->n_items;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -797,7 +820,7 @@ __global__ void __launch_bounds__(WD_NPB) serve_kernel(const ServeTable* __restr
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         float fr, fi;
-                        pair_mixed(etab, qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
+                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
                         br += fr;
                         bi += fi;
                     }
