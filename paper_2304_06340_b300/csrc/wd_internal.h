@@ -190,6 +190,11 @@ struct ServeReq {
     const double* W;        // weights for this request's s
     const double* nu;       // sphere transform (re, im)
     double* blockD;         // per-node-block partial sums of this request
+    const double* rad;      // mixed path, ball rule: radii and unit directions (else null)
+    const double* dir;
+    int n_rad;
+    int n_rg;               // radius groups (node block nb = direction group * n_rg + radius group)
+    int64_t n_dir;
 };
 struct ServeItem {
     int req;                // slot in the request table

@@ -523,10 +523,15 @@ struct __align__(16) RadRec {
     float l2;            // gamma / 2, low part
     float R[6];          // real tail coefficients R1..R6, times 2
     float I[5];          // imaginary tail coefficients I0..I4, times 2
-    float d1, d2;        // omega.e1, omega.e2
-    float pad[2];
+    // divided-difference branch, per unit radius: phase offsets of the two
+    // first differences about the centroid (turns), their half gaps, and
+    // 2 / (largest gap); the case (which vertex pair has the largest gap)
+    // does not depend on r
+    float oP, oQ, hP, hQ;
+    float iD2;
+    float pad[3];
 };
-static_assert(sizeof(RadRec) == 80, "RadRec layout");
+static_assert(sizeof(RadRec) == 96, "RadRec layout");
 
 __device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __restrict__ dir, int64_t n_dir,
                                             int64_t d, RadRec& o)
@@ -543,9 +548,9 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __re
     const float fx = (float)wx, fy = (float)wy, fz = (float)wz;
     const float d1 = fmaf(fx, t.e1[0], fmaf(fy, t.e1[1], fz * t.e1[2]));
     const float d2 = fmaf(fx, t.e2[0], fmaf(fy, t.e2[1], fz * t.e2[2]));
-    o.d1 = d1;
-    o.d2 = d2;
-    o.gmax0 = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d2 - d1)));
+    const float d3 = d2 - d1;
+    const float a1 = fabsf(d1), a2 = fabsf(d2), a3 = fabsf(d3);
+    o.gmax0 = fmaxf(a1, fmaxf(a2, a3));
     o.g2 = 0.5f * t.gam;  // exact
     o.l2 = 0.5f * t.gam_lo;
     const float ya = -(d1 + d2) * (1.0f / 3.0f);
@@ -570,7 +575,39 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __re
     o.I[4] = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
     for (int k = 0; k < 6; ++k) o.R[k] *= 2.0f;  // exact
     for (int k = 0; k < 5; ++k) o.I[k] *= 2.0f;
-    o.pad[0] = o.pad[1] = 0.0f;
+    // largest gap: A = (a, c) with d2, B = (a, b) with d1, C = (b, c) with d3,
+    // as in pair_mixed_divdiff
+    const bool caseA = (a2 >= a1) && (a2 >= a3);
+    const bool caseB = !caseA && (a1 >= a3);
+    const bool caseC = !caseA && !caseB;
+    const float inv4pi = 0.0795774715459476679f;
+    o.oP = caseC ? -inv4pi * yb : -inv4pi * ya;
+    o.hP = caseC ? 0.5f * d2 : 0.5f * d3;
+    o.oQ = caseB ? -inv4pi * yb : -inv4pi * yc;
+    o.hQ = caseB ? 0.5f * d2 : 0.5f * d1;
+    const float D0 = caseA ? d2 : (caseB ? d1 : d3);
+    o.iD2 = D0 != 0.0f ? 2.0f / D0 : 0.0f;  // gmax0 = 0 never takes this branch
+    o.pad[0] = o.pad[1] = o.pad[2] = 0.0f;
+}
+
+// Divided-difference branch of the radial kernel: the per-node version
+// (pair_mixed_divdiff) with its radius-independent choices taken from the
+// record; rinv = 1/r. Returns gamma G.
+__device__ __forceinline__ void radial_divdiff(const TabEntry* __restrict__ tl, float tau, float tlo, float r,
+                                               float rinv, const RadRec& t, float& fr, float& fi)
+{
+    float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
+    expm_turns(tl, fmaf(r, t.oP, tau), tlo, cP, sP);
+    expm_turns(tl, fmaf(r, t.oQ, tau), tlo, cQ, sQ);
+    const float scP = sinc32(r * t.hP), scQ = sinc32(r * t.hQ);
+    // 2 G = i (S_P - S_Q) (2 / D)
+    const float dr = cP * scP - cQ * scQ;
+    const float di = sP * scP - sQ * scQ;
+    const float inv = t.iD2 * rinv;
+    const float gr = -di * inv;
+    const float gi = dr * inv;
+    fr = fmaf(t.g2, gr, t.l2 * gr);  // (gamma/2)(2 G), gamma as a float pair
+    fi = fmaf(t.g2, gi, t.l2 * gi);
 }
 
 // Taylor branch end for the radial kernel, with the doubled tail 2 (sr + i si)
@@ -591,6 +628,111 @@ __device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__
     fi = fmaf(g2, s, fmaf(g2, ti, l2 * s));
 }
 
+// One thread's node in a radial node block: block nb covers directions
+// [dg WD_RAD_ND, +WD_RAD_ND) x radii [rg WD_RAD_NR, +WD_RAD_NR); thread t
+// takes direction t / WD_RAD_NR (warp-uniform) and radius t % WD_RAD_NR.
+struct RadThread {
+    int64_t dg, node;
+    int dl;
+    bool dir_ok, active;
+    float rh, rlo;   // radius as a float pair
+    float rho, r3;   // r^2, r^3
+    float thr;       // Taylor branch while gmax0 < thr = DELTA / r
+    float rinv;      // 1 / r
+    float dith;      // the node's phase dither
+};
+
+__device__ __forceinline__ RadThread radial_thread(const double* __restrict__ rad, int n_rad, int64_t n_dir,
+                                                   int64_t nb, int n_rg)
+{
+    RadThread h;
+    h.dl = threadIdx.x / WD_RAD_NR;
+    const int rl = threadIdx.x % WD_RAD_NR;
+    h.dg = nb / n_rg;
+    const int rg = (int)(nb - h.dg * n_rg);
+    const int64_t d = h.dg * WD_RAD_ND + h.dl;
+    const int ir = rg * WD_RAD_NR + rl;
+    h.dir_ok = d < n_dir;
+    h.active = h.dir_ok && ir < n_rad;
+    h.node = h.active ? (int64_t)ir * n_dir + d : 0;
+    const double r = h.active ? rad[ir] : 0.0;
+    h.rh = (float)r;
+    h.rlo = (float)(r - (double)h.rh);
+    h.rho = (float)(r * r);
+    h.r3 = (float)(r * r * r);
+    h.thr = h.active ? (float)((double)kDelta32 / r) : 3.402823466e38f;
+    h.rinv = h.active ? (float)(1.0 / r) : 0.0f;
+    h.dith = node_dither(h.node);
+    return h;
+}
+
+// Sum of F_T over the triangle records [t0, t1) at this thread's node, in
+// tiles of WD_RAD_TILE triangles: the block first fills the tile's
+// (direction, triangle) records, then every thread runs over its direction's
+// row. Called by every thread of the block (barriers inside).
+__device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const TabEntry* __restrict__ tl,
+                                           const TriRecF* __restrict__ tris, int64_t t0, int64_t t1,
+                                           const double* __restrict__ dir, int64_t n_dir, const RadThread& h,
+                                           double& acc_r, double& acc_i)
+{
+    acc_r = 0.0;
+    acc_i = 0.0;
+    for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
+        const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
+        const int cnt8 = (cnt + 7) & ~7;
+        __syncthreads();
+        // records for WD_RAD_ND directions x cnt8 triangles (zero padding: gamma = 0)
+        for (int i = threadIdx.x; i < WD_RAD_ND * WD_RAD_TILE; i += WD_NPB) {
+            const int di = i / WD_RAD_TILE, j = i % WD_RAD_TILE;
+            const int64_t dd = h.dg * WD_RAD_ND + di;
+            if (j >= cnt8) continue;
+            RadRec o;
+            if (j < cnt && dd < n_dir) {
+                const TriRecF tr = tris[tb + j];
+                make_radrec(tr, dir, n_dir, dd, o);
+            } else {
+                o = RadRec{};
+            }
+            tile[di][j] = o;
+        }
+        __syncthreads();
+        if (!h.dir_ok) continue;  // warp-uniform
+        const RadRec* rec = tile[h.dl];
+        // plain float32 sums over groups of 8 pairs (dithered phases: random
+        // roundings), Kahan across groups
+        Kahan kr, ki;
+        for (int j = 0; j < cnt8; j += 8) {
+            float br = 0.0f, bi = 0.0f;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const RadRec& t = rec[j + jj];
+                // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
+                const float P = h.rh * t.dmh;
+                const float e = fmaf(h.rh, t.dmh, -P);
+                const float lo = fmaf(h.rh, t.dml, fmaf(h.rlo, t.dmh, e));
+                const float tau = (P - rintf(P)) - h.dith;
+                float fr, fi;
+                if (t.gmax0 < h.thr) {
+                    const float rho = h.rho;
+                    float sr = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
+                    sr = fmaf(sr, rho, t.R[0]) * rho;
+                    float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
+                    si = fmaf(si, rho, t.I[0]) * h.r3;
+                    taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi);
+                } else {
+                    radial_divdiff(tl, tau, lo, h.rh, h.rinv, t, fr, fi);
+                }
+                br += fr;
+                bi += fi;
+            }
+            kr.add(br);
+            ki.add(bi);
+        }
+        acc_r += kr.value();
+        acc_i += ki.value();
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a, const PairPlan p)
 {
@@ -600,84 +742,16 @@ __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a
     __shared__ TabEntry etab[kTab * kTabRep];
     fill_exp_table(etab);  // visible after the first tile barrier
     const TabEntry* tl = exp_table_lane(etab);
-
-    const int dl = threadIdx.x / WD_RAD_NR;  // direction within the block (warp-uniform)
-    const int rl = threadIdx.x % WD_RAD_NR;
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
         const int64_t nb = item / p.nchunks;
         const int chunk = (int)(item - nb * p.nchunks);
-        const int64_t dg = nb / p.n_rg;
-        const int rg = (int)(nb - dg * p.n_rg);
-        const int64_t d = dg * WD_RAD_ND + dl;
-        const int ir = rg * WD_RAD_NR + rl;
-        const bool dir_ok = d < a.n_dir;
-        const bool active = dir_ok && ir < a.n_rad;
-        const int64_t node = active ? (int64_t)ir * a.n_dir + d : 0;
-        // this thread's radius: float pair, r^2, r^3, and the Taylor bound on gmax0
-        const double r = active ? a.rad[ir] : 0.0;
-        const float rh = (float)r, rlo = (float)(r - (double)rh);
-        const float rho = (float)(r * r), r3 = (float)(r * r * r);
-        const float thr = active ? (float)((double)kDelta32 / r) : 3.402823466e38f;
-        const float dith = node_dither(node);
-
+        const RadThread h = radial_thread(a.rad, a.n_rad, a.n_dir, nb, p.n_rg);
         const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
         int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
         if (t1 > a.T) t1 = a.T;
-        double acc_r = 0.0, acc_i = 0.0;
-        for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
-            const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
-            const int cnt8 = (cnt + 7) & ~7;
-            __syncthreads();
-            // records for WD_RAD_ND directions x cnt8 triangles (zero padding: gamma = 0)
-            for (int i = threadIdx.x; i < WD_RAD_ND * WD_RAD_TILE; i += WD_NPB) {
-                const int di = i / WD_RAD_TILE, j = i % WD_RAD_TILE;
-                const int64_t dd = dg * WD_RAD_ND + di;
-                if (j >= cnt8) continue;
-                RadRec o;
-                if (j < cnt && dd < a.n_dir) {
-                    const TriRecF tr = static_cast<const TriRecF*>(a.tris)[tb + j];
-                    make_radrec(tr, a.dir, a.n_dir, dd, o);
-                } else {
-                    o = RadRec{};
-                }
-                tile[di][j] = o;
-            }
-            __syncthreads();
-            if (!dir_ok) continue;  // warp-uniform
-            const RadRec* rec = tile[dl];
-            // plain float32 sums over groups of 8 pairs (dithered phases: random
-            // roundings), Kahan across groups
-            Kahan kr, ki;
-            for (int j = 0; j < cnt8; j += 8) {
-                float br = 0.0f, bi = 0.0f;
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const RadRec& t = rec[j + jj];
-                    // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
-                    const float P = rh * t.dmh;
-                    const float e = fmaf(rh, t.dmh, -P);
-                    const float lo = fmaf(rh, t.dml, fmaf(rlo, t.dmh, e));
-                    const float tau = (P - rintf(P)) - dith;
-                    float fr, fi;
-                    if (t.gmax0 < thr) {
-                        float sr = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
-                        sr = fmaf(sr, rho, t.R[0]) * rho;
-                        float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
-                        si = fmaf(si, rho, t.I[0]) * r3;
-                        taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi);
-                    } else {
-                        pair_mixed_divdiff(tl, tau, lo, rh * t.d1, rh * t.d2, 2.0f * t.g2, 2.0f * t.l2, fr, fi);
-                    }
-                    br += fr;
-                    bi += fi;
-                }
-                kr.add(br);
-                ki.add(bi);
-            }
-            acc_r += kr.value();
-            acc_i += ki.value();
-        }
-        node_epilogue<true, MODE>(a, p, nb, chunk, node, active, dith, acc_r, acc_i, red, s_last);
+        double acc_r, acc_i;
+        radial_sum(tile, tl, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
+        node_epilogue<true, MODE>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red, s_last);
     }
 }
 
@@ -764,20 +838,44 @@ int resident_for(wd_ctx* ctx, int precision, int mode)
 // block is the same as in pair_kernel with one triangle chunk, so a request's
 // result does not depend on what else is in the batch.
 template <bool MIXED>
-__global__ void __launch_bounds__(WD_NPB) serve_kernel(const ServeTable* __restrict__ head,
+__global__ void __launch_bounds__(WD_NPB, 4) serve_kernel(const ServeTable* __restrict__ head,
                                                        const ServeReq* __restrict__ reqs,
                                                        const ServeItem* __restrict__ items)
 {
     using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
-    __shared__ __align__(16) Rec tile[WD_TILE];
+    // per-node triangle tile or, for ball rules in the mixed path, the radial record tile
+    constexpr size_t kTileBytes = sizeof(Rec) * WD_TILE > sizeof(RadRec) * WD_RAD_ND * WD_RAD_TILE
+                                      ? sizeof(Rec) * WD_TILE
+                                      : sizeof(RadRec) * WD_RAD_ND * WD_RAD_TILE;
+    __shared__ __align__(16) unsigned char tbuf[kTileBytes];
+    Rec* tile = reinterpret_cast<Rec*>(tbuf);
     __shared__ double red[WD_NPB / 32];
-    __shared__ TabEntry etab[kTab * kTabRep];
+    __shared__ TabEntry etab[MIXED ? kTab * kTabRep : 1];
     if (MIXED) fill_exp_table(etab);
     const int n_items = head->n_items;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const ServeItem item = items[it];
         const ServeReq rq = reqs[item.req];
         const int64_t n = rq.n;
+        if (MIXED && rq.rad) {  // block-uniform
+            const RadThread h = radial_thread(rq.rad, rq.n_rad, rq.n_dir, item.nb, rq.n_rg);
+            double mr, mi;
+            radial_sum(reinterpret_cast<RadRec(*)[WD_RAD_TILE]>(tbuf), exp_table_lane(etab),
+                       static_cast<const TriRecF*>(rq.rec), 0, rq.T, rq.dir, rq.n_dir, h, mr, mi);
+            double sd, cd;
+            sincospi(2.0 * (double)h.dith, &sd, &cd);
+            const double r_ = mr * cd + mi * sd;
+            mi = mi * cd - mr * sd;
+            mr = r_;
+            double term = 0.0;
+            if (h.active) {
+                const double dr = mr - rq.nu[2 * h.node], di = mi - rq.nu[2 * h.node + 1];
+                term = rq.W[h.node] * (dr * dr + di * di);
+            }
+            const double bsum = block_sum(term, red);
+            if (threadIdx.x == 0) rq.blockD[item.nb] = bsum;
+            continue;
+        }
         const int64_t node = (int64_t)item.nb * WD_NPB + threadIdx.x;
         const bool active = node < n;
         const double x = active ? rq.xi[node] : 0.0;

@@ -335,6 +335,12 @@ void worker_main(wd_server* sv)
                 q.T = T;
                 q.xi = re.rule->d_xi;
                 q.n = re.rule->n_eval;
+                const bool radial = sv->cfg.precision == WD_MIXED && re.rule->d_rad;
+                q.rad = radial ? re.rule->d_rad : nullptr;
+                q.dir = radial ? re.rule->d_dir : nullptr;
+                q.n_rad = re.rule->n_rad;
+                q.n_rg = (re.rule->n_rad + WD_RAD_NR - 1) / WD_RAD_NR;
+                q.n_dir = re.rule->n_dir;
                 q.W = re.W[r->s];
                 q.nu = re.nu;
                 q.blockD = reinterpret_cast<double*>(
@@ -480,7 +486,14 @@ extern "C" wd_status wd_serve_submit(wd_server* sv, const wd_mesh* m, double s, 
     r->tris.assign(m->tris, m->tris + 3 * m->n_tris);
     r->s = s;
     r->rule = rule;
-    r->n_nb = (int)((sv->rules[rule].rule->n_eval + WD_NPB - 1) / WD_NPB);
+    {
+        // node blocks: radius x direction blocks for ball rules in the mixed path
+        const wd_rule* ru = sv->rules[rule].rule;
+        if (sv->cfg.precision == WD_MIXED && ru->d_rad)
+            r->n_nb = (int)(((ru->n_dir + WD_RAD_ND - 1) / WD_RAD_ND) * ((ru->n_rad + WD_RAD_NR - 1) / WD_RAD_NR));
+        else
+            r->n_nb = (int)((ru->n_eval + WD_NPB - 1) / WD_NPB);
+    }
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->fatal != WD_OK) {
         delete r;
