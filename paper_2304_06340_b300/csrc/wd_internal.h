@@ -59,14 +59,16 @@ struct wd_rule {
     int64_t n_eval = 0, n_total = 0;
     std::vector<double> h_xi;         // SoA, 3 * n_eval
     std::vector<double> h_wg;         // s-free weights
-    std::vector<double> h_rad, h_dir; // ball rules: radii and unit directions (SoA)
+    std::vector<double> h_rad;        // ball rules: radii
+    std::vector<float> h_dir;         // ball rules: directions, layout of d_dir
     double* d_xi = nullptr;           // SoA on the device
     double* d_wg = nullptr;
-    // ball rules only: node k = rad[k / n_dir] * dir[k % n_dir] (radius outer)
+    // ball rules only: node k = rad[k / n_dir] * omega[k % n_dir] (radius outer)
     int n_rad = 0;
     int64_t n_dir = 0;
     double* d_rad = nullptr;          // radial nodes, n_rad
-    double* d_dir = nullptr;          // unit directions, SoA 3 * n_dir
+    float* d_dir = nullptr;           // per direction, SoA 9 * n_dir: omega (x, y, z) in float32,
+                                      // then omega / 2 pi as float pairs: high (x, y, z), low (x, y, z)
     std::map<double, double*> w_cache;                  // s -> W_k
     std::map<std::array<double, 4>, double*> nu_cache;  // (radius, center) -> nu^ (re, im interleaved)
 };
@@ -131,8 +133,8 @@ struct PairArgs {
     double* out = nullptr;        // MODE_DIST: D; MODE_FT: re[n]
     double* out_im = nullptr;     // MODE_FT: im[n]
     double* resid = nullptr;      // MODE_RESID: 2 W_k (mu^ - nu^)(xi_k), (re, im) interleaved
-    const double* rad = nullptr;  // radial plan: radii (n_rad) and unit directions (SoA, n_dir)
-    const double* dir = nullptr;
+    const double* rad = nullptr;  // radial plan: radii (n_rad) and directions (wd_rule::d_dir layout)
+    const float* dir = nullptr;
     int n_rad = 0;
     int64_t n_dir = 0;
 };
@@ -190,8 +192,8 @@ struct ServeReq {
     const double* W;        // weights for this request's s
     const double* nu;       // sphere transform (re, im)
     double* blockD;         // per-node-block partial sums of this request
-    const double* rad;      // mixed path, ball rule: radii and unit directions (else null)
-    const double* dir;
+    const double* rad;      // mixed path, ball rule: radii and directions (wd_rule::d_dir layout; else null)
+    const float* dir;
     int n_rad;
     int n_rg;               // radius groups (node block nb = direction group * n_rg + radius group)
     int64_t n_dir;

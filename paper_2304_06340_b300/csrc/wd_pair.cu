@@ -513,7 +513,8 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
 // the same terms (h_n to n = 12) as the per-node kernel, regrouped by powers of
 // r. A block covers WD_RAD_ND directions x WD_RAD_NR radii; for each tile of
 // triangles it first computes one record of rates and coefficients per
-// (direction, triangle), in float64 for the phase rate, then every thread runs
+// (direction, triangle), in float32 (float pairs for the phase rate: the
+// float64 pipe of this GPU is too narrow for it), then every thread runs
 // over the tile with its own radius. A warp holds 32 radii of one direction,
 // so the record loads are broadcasts.
 struct __align__(16) RadRec {
@@ -533,19 +534,31 @@ struct __align__(16) RadRec {
 };
 static_assert(sizeof(RadRec) == 96, "RadRec layout");
 
-__device__ __forceinline__ void make_radrec(const TriRecF& t, const double* __restrict__ dir, int64_t n_dir,
+__device__ __forceinline__ void make_radrec(const TriRecF& t, const float* __restrict__ dir, int64_t n_dir,
                                             int64_t d, RadRec& o)
 {
-    const double inv2pi = 0.15915494309189533576888376337251;
-    const double wx = dir[d], wy = dir[n_dir + d], wz = dir[2 * n_dir + d];
-    // centroid (mh + ml is exact in float64)
-    const double mx = (double)t.mh[0] + (double)t.ml[0];
-    const double my = (double)t.mh[1] + (double)t.ml[1];
-    const double mz = (double)t.mh[2] + (double)t.ml[2];
-    const double dm = fma(wx, mx, fma(wy, my, wz * mz)) * inv2pi;
-    o.dmh = (float)dm;
-    o.dml = (float)(dm - (double)o.dmh);
-    const float fx = (float)wx, fy = (float)wy, fz = (float)wz;
+    const float fx = dir[d], fy = dir[n_dir + d], fz = dir[2 * n_dir + d];
+    const float hx = dir[3 * n_dir + d], hy = dir[4 * n_dir + d], hz = dir[5 * n_dir + d];
+    const float lx = dir[6 * n_dir + d], ly = dir[7 * n_dir + d], lz = dir[8 * n_dir + d];
+    // omega.m / 2 pi in float-pair arithmetic (relative error ~2^-46): exact
+    // high products, their exact two-sums, and the first-order low terms
+    const float u0 = hx * t.mh[0], u1 = hy * t.mh[1], u2 = hz * t.mh[2];
+    const float v0 = fmaf(hx, t.mh[0], -u0), v1 = fmaf(hy, t.mh[1], -u1), v2 = fmaf(hz, t.mh[2], -u2);
+    const float s1 = u0 + u1;
+    float bv = s1 - u0;
+    float err = (u0 - (s1 - bv)) + (u1 - bv);
+    const float s2 = s1 + u2;
+    bv = s2 - s1;
+    err += (s1 - (s2 - bv)) + (u2 - bv);
+    float lo = err + (v0 + v1 + v2);
+    lo = fmaf(hx, t.ml[0], lo);
+    lo = fmaf(hy, t.ml[1], lo);
+    lo = fmaf(hz, t.ml[2], lo);
+    lo = fmaf(lx, t.mh[0], lo);
+    lo = fmaf(ly, t.mh[1], lo);
+    lo = fmaf(lz, t.mh[2], lo);
+    o.dmh = s2 + lo;
+    o.dml = lo - (o.dmh - s2);
     const float d1 = fmaf(fx, t.e1[0], fmaf(fy, t.e1[1], fz * t.e1[2]));
     const float d2 = fmaf(fx, t.e2[0], fmaf(fy, t.e2[1], fz * t.e2[2]));
     const float d3 = d2 - d1;
@@ -672,7 +685,7 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
 // row. Called by every thread of the block (barriers inside).
 __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const TabEntry* __restrict__ tl,
                                            const TriRecF* __restrict__ tris, int64_t t0, int64_t t1,
-                                           const double* __restrict__ dir, int64_t n_dir, const RadThread& h,
+                                           const float* __restrict__ dir, int64_t n_dir, const RadThread& h,
                                            double& acc_r, double& acc_i)
 {
     acc_r = 0.0;

@@ -110,9 +110,9 @@ wd_status upload_rule(wd_ctx* ctx, wd_rule* r)
     }
     if (!r->h_rad.empty()) {
         WD_CUDA(cudaMalloc(&r->d_rad, sizeof(double) * r->h_rad.size()));
-        WD_CUDA(cudaMalloc(&r->d_dir, sizeof(double) * r->h_dir.size()));
+        WD_CUDA(cudaMalloc(&r->d_dir, sizeof(float) * r->h_dir.size()));
         WD_CUDA(cudaMemcpy(r->d_rad, r->h_rad.data(), sizeof(double) * r->h_rad.size(), cudaMemcpyHostToDevice));
-        WD_CUDA(cudaMemcpy(r->d_dir, r->h_dir.data(), sizeof(double) * r->h_dir.size(), cudaMemcpyHostToDevice));
+        WD_CUDA(cudaMemcpy(r->d_dir, r->h_dir.data(), sizeof(float) * r->h_dir.size(), cudaMemcpyHostToDevice));
     }
     r->ctx = ctx;
     return WD_OK;
@@ -269,14 +269,19 @@ extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_r
     r->n_rad = d->n_r;
     r->n_dir = (int64_t)n_u * d->n_azim;
     r->h_rad.resize(d->n_r);
-    r->h_dir.resize(3 * r->n_dir);
+    r->h_dir.resize(9 * r->n_dir);
     for (int i = 0; i < d->n_r; ++i) r->h_rad[i] = (double)(half_R * (1.0L + xr[i]));
     for (int j = 0, kd = 0; j < n_u; ++j) {
         const long double u = xu[u0 + j], sn = sqrtl(1.0L - u * u);
         for (int m = 0; m < d->n_azim; ++m, ++kd) {
-            r->h_dir[kd] = (double)(sn * cph[m]);
-            r->h_dir[r->n_dir + kd] = (double)(sn * sph[m]);
-            r->h_dir[2 * r->n_dir + kd] = (double)u;
+            const long double w[3] = {sn * cph[m], sn * sph[m], u};
+            for (int c = 0; c < 3; ++c) {
+                const long double t = w[c] / (2.0L * kPi);
+                const float hi = (float)t;
+                r->h_dir[c * r->n_dir + kd] = (float)w[c];
+                r->h_dir[(3 + c) * r->n_dir + kd] = hi;
+                r->h_dir[(6 + c) * r->n_dir + kd] = (float)(t - (long double)hi);
+            }
         }
     }
     int64_t k = 0;
