@@ -40,9 +40,9 @@ N_FP32_PER_PAIR = 60
 N_MUFU_PER_PAIR = 6
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
 # DRAM bytes (read + write) of one mixed pair-kernel launch on the n = 64 sweep
-# query, from ncu (profiles/pair_kernel_mixed_sweep_n64.md); None once the
+# query, from ncu (profiles/pair_kernel_radial_sweep_n64.md); None once the
 # kernel changes after that capture.
-PAIR_KERNEL_TRAFFIC_N64 = None  # kernel changed after the capture; re-measure
+PAIR_KERNEL_TRAFFIC_N64 = 48.36e6
 
 
 def parse():
@@ -458,9 +458,10 @@ def main():
     roof = {"bound": "alu", "achieved": pair_rate / 1e9, "peak": peak / 1e9, "unit": UNIT,
             "frac": pair_rate / peak,
             "traffic": PAIR_KERNEL_TRAFFIC_N64 if prec == wd.WD_MIXED else None,
-            "traffic_note": "dram read+write bytes of the n=64 launch (ncu); algorithmic bytes per launch "
-                            "are the rule (32 B/node) and the mesh records (64 B/triangle), 62 MB",
-            "kernel": "pair_kernel (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
+            "traffic_note": "dram read+write bytes of the n=64 launch of pair_kernel_radial (ncu, "
+                            "profiles/pair_kernel_radial_sweep_n64.md); algorithmic bytes of that launch: W and nu^ "
+                            "per node (24 B x 1,769,472) + mesh records (64 B x 81,920) = 47.7 MB",
+            "kernel": "pair_kernel_radial (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
             "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
                           % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
                              N_MUFU_PER_PAIR)}
