@@ -507,6 +507,286 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __
     }
 }
 
+// ------------------------------------------------------------------ radial mixed adjoint (ball rules)
+// Ball-rule nodes are xi = r omega, so per (direction, triangle) the phase,
+// the gaps and the Taylor polynomials are fixed rates and coefficients in r,
+// as in the radial pair kernel. One thread per triangle runs over the
+// directions of its chunk; for each direction it forms, in registers, the
+// phase rate omega.m / 2 pi (float pair), the tail T = Psi - 1/2 and its
+// partials T_p, T_q as polynomials in rho = r^2:
+//     T   = rho (R1 + ... + rho^5 R6) + i r^3 (I0 + ... + rho^4 I4),
+//     T_p = (-1/24 + rho a1 + ... + rho^5 a5) + i r^3 (b0 + ... + rho^3 b3),
+//     T_q = r^3 (c0 + ... + rho^3 c3) + i (1/120 + rho e1 + ... + rho^4 e4),
+// then loops over the radii (node data staged per direction in shared memory).
+// With Z = conj(r'_k) exp(-i t_m) and y_b = r yb0, dq/dg1 = r^2 dq1_0 (and
+// y_c, dq/dg2 likewise), Psi_1 = T_p y_b + T_q dq/dg1 gives
+//     sum_r rho_1 r = yb0 sum_r rho Re(Z T_p) + dq1_0 sum_r r^3 Re(Z T_q),
+// so the Taylor branch needs two derivative sums per direction. In the
+// largest-gap branch the case constants and D = r D0 factor out of the radius
+// sum, leaving five sums. The per-direction sums, times omega, go into ten
+// float64 per-triangle totals kept in shared memory.
+constexpr int ADJ_RMAX = 256;  // radii per direction the radial adjoint stages
+
+struct __align__(16) AdjRad {
+    float rh, rlo;  // radius as a float pair
+    float rho, r3;  // r^2, r^3
+    float rinv;     // 1 / r
+    float thr;      // Taylor branch while gmax0 < thr = DELTA / r
+    float pad[2];
+};
+
+// Residual rotated by the node's dither, direction-major: nd[d n_rad + ir] =
+// (Re, Im of r_k exp(2 pi i d_k), d_k, 0) for node k = ir n_dir + d.
+__global__ void adjoint_prep_radial(const double* __restrict__ resid, int n_rad, int64_t n_dir,
+                                    float4* __restrict__ nd)
+{
+    const int64_t n = (int64_t)n_rad * n_dir;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ir = k / n_dir, d = k - ir * n_dir;
+        const float dith = node_dither(k);
+        double sd, cd;
+        sincospi(2.0 * (double)dith, &sd, &cd);
+        const double r0 = resid[2 * k], r1 = resid[2 * k + 1];
+        nd[d * n_rad + ir] = make_float4((float)(r0 * cd - r1 * sd), (float)(r0 * sd + r1 * cd), dith, 0.0f);
+    }
+}
+
+// Per-(direction, triangle) quantities of the radial adjoint.
+struct AdjDirTri {
+    float dmh, dml, gmax0;
+    float R[6], I[5];            // T
+    float a[5], b[4], c[4], e[4];  // T_p, T_q (constant terms -1/24 and 1/120 implicit)
+    float oPt, oQt, hP0, hQ0;    // largest-gap branch: offsets (turns) and half gaps per unit radius
+};
+
+__device__ __forceinline__ void adj_dirtri(const TriRecF& t, const float* __restrict__ dir, int64_t n_dir, int64_t d,
+                                           AdjDirTri& o, float& d1, float& d2)
+{
+    const float fx = dir[d], fy = dir[n_dir + d], fz = dir[2 * n_dir + d];
+    const float hx = dir[3 * n_dir + d], hy = dir[4 * n_dir + d], hz = dir[5 * n_dir + d];
+    const float lx = dir[6 * n_dir + d], ly = dir[7 * n_dir + d], lz = dir[8 * n_dir + d];
+    // omega.m / 2 pi as a float pair (as in the radial pair kernel)
+    const float u0 = hx * t.mh[0], u1 = hy * t.mh[1], u2 = hz * t.mh[2];
+    const float v0 = fmaf(hx, t.mh[0], -u0), v1 = fmaf(hy, t.mh[1], -u1), v2 = fmaf(hz, t.mh[2], -u2);
+    const float s1 = u0 + u1;
+    float bv = s1 - u0;
+    float err = (u0 - (s1 - bv)) + (u1 - bv);
+    const float s2 = s1 + u2;
+    bv = s2 - s1;
+    err += (s1 - (s2 - bv)) + (u2 - bv);
+    float lo = err + (v0 + v1 + v2);
+    lo = fmaf(hx, t.ml[0], lo);
+    lo = fmaf(hy, t.ml[1], lo);
+    lo = fmaf(hz, t.ml[2], lo);
+    lo = fmaf(lx, t.mh[0], lo);
+    lo = fmaf(ly, t.mh[1], lo);
+    lo = fmaf(lz, t.mh[2], lo);
+    o.dmh = s2 + lo;
+    o.dml = lo - (o.dmh - s2);
+    d1 = fmaf(fx, t.e1[0], fmaf(fy, t.e1[1], fz * t.e1[2]));
+    d2 = fmaf(fx, t.e2[0], fmaf(fy, t.e2[1], fz * t.e2[2]));
+    const float d3 = d2 - d1;
+    const float a1 = fabsf(d1), a2 = fabsf(d2), a3 = fabsf(d3);
+    o.gmax0 = fmaxf(a1, fmaxf(a2, a3));
+    const float ya = -(d1 + d2) * (1.0f / 3.0f);
+    const float yb = (2.0f * d1 - d2) * (1.0f / 3.0f);
+    const float yc = (2.0f * d2 - d1) * (1.0f / 3.0f);
+    const float p0 = (d1 * d1 - d1 * d2 + d2 * d2) * (1.0f / 3.0f);
+    const float A0 = fmaf(d1, d1 - d2, d2 * d2);
+    const float q0 = ya * yb * yc;
+    const float q02 = q0 * q0;
+    const float p2 = p0 * p0, p3 = p2 * p0, p4 = p2 * p2;
+    // T: as in the radial pair kernel (not doubled)
+    o.R[0] = fmaf(A0, -1.388888899e-02f, A0 * 1.034802868e-10f);
+    o.R[1] = p2 * (1.0f / 720.0f);
+    o.R[2] = -(p3 + q02) * (1.0f / 40320.0f);
+    o.R[3] = fmaf(3.0f * q02, p0, p4) * (1.0f / 3628800.0f);
+    o.R[4] = -fmaf(6.0f * q02, p2, p4 * p0) * (1.0f / 479001600.0f);
+    o.R[5] = fmaf(10.0f * q02, p3, fmaf(p3, p3, q02 * q02)) * (1.0f / 87178291200.0f);
+    o.I[0] = q0 * (1.0f / 120.0f);
+    o.I[1] = -2.0f * q0 * p0 * (1.0f / 5040.0f);
+    o.I[2] = 3.0f * q0 * p2 * (1.0f / 362880.0f);
+    o.I[3] = -q0 * fmaf(4.0f, p3, q02) * (1.0f / 39916800.0f);
+    o.I[4] = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
+    // Re T_p = -1/24 + p dre(p) + q^2 drq(p), in rho (a_j multiplies rho^j)
+    o.a[0] = 2.0f * p0 * (1.0f / 720.0f);
+    o.a[1] = -3.0f * p2 * (1.0f / 40320.0f);
+    o.a[2] = fmaf(4.0f, p3, 3.0f * q02) * (1.0f / 3628800.0f);
+    o.a[3] = -fmaf(5.0f, p4, 12.0f * q02 * p0) * (1.0f / 479001600.0f);
+    o.a[4] = fmaf(6.0f, p4 * p0, 30.0f * q02 * p2) * (1.0f / 87178291200.0f);
+    // Im T_p = q (dim(p) + 4 q^2 / 13!) = r^3 (b0 + rho b1 + rho^2 b2 + rho^3 b3)
+    o.b[0] = -2.0f * q0 * (1.0f / 5040.0f);
+    o.b[1] = 6.0f * q0 * p0 * (1.0f / 362880.0f);
+    o.b[2] = -12.0f * q0 * p2 * (1.0f / 39916800.0f);
+    o.b[3] = q0 * fmaf(20.0f, p3, 4.0f * q02) * (1.0f / 6227020800.0f);
+    // Re T_q = q (2 rq(p) + 4 q^2 / 14!) = r^3 (c0 + ... + rho^3 c3)
+    o.c[0] = -2.0f * q0 * (1.0f / 40320.0f);
+    o.c[1] = 6.0f * q0 * p0 * (1.0f / 3628800.0f);
+    o.c[2] = -12.0f * q0 * p2 * (1.0f / 479001600.0f);
+    o.c[3] = q0 * fmaf(20.0f, p3, 4.0f * q02) * (1.0f / 87178291200.0f);
+    // Im T_q = im(p) + 3 q^2 iq(p) = 1/120 + rho e1 + ... + rho^4 e4
+    o.e[0] = -2.0f * p0 * (1.0f / 5040.0f);
+    o.e[1] = 3.0f * p2 * (1.0f / 362880.0f);
+    o.e[2] = -fmaf(4.0f, p3, 3.0f * q02) * (1.0f / 39916800.0f);
+    o.e[3] = fmaf(5.0f, p4, 12.0f * q02 * p0) * (1.0f / 6227020800.0f);
+    // largest-gap branch: A = (a, c) with d2, B = (a, b) with d1, C = (b, c) with d3
+    const bool caseA = (a2 >= a1) && (a2 >= a3);
+    const bool caseB = !caseA && (a1 >= a3);
+    const bool caseC = !caseA && !caseB;
+    const float inv4pi = 0.0795774715459476679f;
+    o.oPt = caseC ? -inv4pi * yb : -inv4pi * ya;
+    o.hP0 = caseC ? 0.5f * d2 : 0.5f * d3;
+    o.oQt = caseB ? -inv4pi * yb : -inv4pi * yc;
+    o.hQ0 = caseB ? 0.5f * d2 : 0.5f * d1;
+}
+
+__global__ void __launch_bounds__(ADJ_TPB, 4) adjoint_kernel_radial(const TriRecF* __restrict__ rec, int64_t nt,
+                                                                    const float4* __restrict__ nd,
+                                                                    const double* __restrict__ rad, int n_rad,
+                                                                    const float* __restrict__ dir, int64_t n_dir,
+                                                                    const AdjPlan p, double* __restrict__ partial)
+{
+    __shared__ AdjRad rt[ADJ_RMAX];
+    __shared__ float4 sn[ADJ_RMAX];
+    __shared__ double acc[10][ADJ_TPB];
+    __shared__ TabEntry etab[kTab * kTabRep];
+    fill_exp_table(etab);
+    const TabEntry* tl = exp_table_lane(etab);
+    for (int i = threadIdx.x; i < n_rad; i += ADJ_TPB) {
+        const double r = rad[i];
+        AdjRad a;
+        a.rh = (float)r;
+        a.rlo = (float)(r - (double)a.rh);
+        a.rho = (float)(r * r);
+        a.r3 = (float)(r * r * r);
+        a.rinv = (float)(1.0 / r);
+        a.thr = (float)((double)kDeltaAM / r);
+        a.pad[0] = a.pad[1] = 0.0f;
+        rt[i] = a;
+    }
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const int64_t tb = item / p.nchunks;
+        const int chunk = (int)(item - tb * p.nchunks);
+        const int64_t tri = tb * ADJ_TPB + threadIdx.x;
+        const bool active = tri < nt;
+        for (int c = 0; c < 10; ++c) acc[c][threadIdx.x] = 0.0;
+        const int64_t d0 = (int64_t)chunk * p.dirs_per_chunk;
+        int64_t d1e = d0 + p.dirs_per_chunk;
+        if (d1e > n_dir) d1e = n_dir;
+        for (int64_t d = d0; d < d1e; ++d) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < n_rad; i += ADJ_TPB) sn[i] = nd[d * n_rad + i];
+            __syncthreads();
+            if (!active) continue;
+            const TriRecF t = rec[tri];
+            AdjDirTri q;
+            float g1d, g2d;
+            adj_dirtri(t, dir, n_dir, d, q, g1d, g2d);
+            // Taylor-branch sums (1/2 part and tail kept apart) and largest-gap sums
+            float S0h = 0.0f, S0t = 0.0f, Sih = 0.0f, Sit = 0.0f, SA = 0.0f, SB = 0.0f;
+            float xP = 0.0f, yP = 0.0f, xQ = 0.0f, yQ = 0.0f, G0 = 0.0f;
+            for (int ir = 0; ir < n_rad; ++ir) {
+                const AdjRad a = rt[ir];
+                const float4 w = sn[ir];
+                const float rr = w.x, ri = w.y;
+                const float P = a.rh * q.dmh;
+                const float e = fmaf(a.rh, q.dmh, -P);
+                const float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
+                const float tau = (P - rintf(P)) - w.z;
+                if (q.gmax0 < a.thr) {
+                    float c, s;
+                    expm_turns(tl, tau, lo, c, s);
+                    const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
+                    const float rho = a.rho, r3 = a.r3;
+                    float sr = fmaf(fmaf(fmaf(fmaf(q.R[5], rho, q.R[4]), rho, q.R[3]), rho, q.R[2]), rho, q.R[1]);
+                    sr = fmaf(sr, rho, q.R[0]) * rho;
+                    float si = fmaf(fmaf(fmaf(q.I[4], rho, q.I[3]), rho, q.I[2]), rho, q.I[1]);
+                    si = fmaf(si, rho, q.I[0]) * r3;
+                    S0h += Zr;
+                    S0t = fmaf(Zr, sr, fmaf(-Zi, si, S0t));
+                    Sih = fmaf(Zi, a.rh, Sih);
+                    Sit = fmaf(fmaf(Zr, si, Zi * sr), a.rh, Sit);
+                    float Ap = fmaf(fmaf(fmaf(fmaf(q.a[4], rho, q.a[3]), rho, q.a[2]), rho, q.a[1]), rho, q.a[0]);
+                    Ap = fmaf(Ap, rho, -1.0f / 24.0f);
+                    const float Bp = fmaf(fmaf(fmaf(q.b[3], rho, q.b[2]), rho, q.b[1]), rho, q.b[0]) * r3;
+                    const float Cq = fmaf(fmaf(fmaf(q.c[3], rho, q.c[2]), rho, q.c[1]), rho, q.c[0]) * r3;
+                    float Eq = fmaf(fmaf(fmaf(q.e[3], rho, q.e[2]), rho, q.e[1]), rho, q.e[0]);
+                    Eq = fmaf(Eq, rho, 1.0f / 120.0f);
+                    SA = fmaf(rho, fmaf(Zr, Ap, -Zi * Bp), SA);
+                    SB = fmaf(r3, fmaf(Zr, Cq, -Zi * Eq), SB);
+                } else {
+                    float cP, sP, cQ, sQ;
+                    expm_turns(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
+                    expm_turns(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
+                    float scP, dscP, scQ, dscQ;
+                    sincd32(a.rh * q.hP0, scP, dscP);
+                    sincd32(a.rh * q.hQ0, scQ, dscQ);
+                    // X = E sinc(h), Y = i E sinc'(h); x = Re(conj r' X), y = Re(conj r' Y)
+                    const float XPr = cP * scP, XPi = sP * scP, XQr = cQ * scQ, XQi = sQ * scQ;
+                    xP = fmaf(rr, XPr, fmaf(ri, XPi, xP));
+                    xQ = fmaf(rr, XQr, fmaf(ri, XQi, xQ));
+                    yP = fmaf(dscP, fmaf(ri, cP, -rr * sP), yP);
+                    yQ = fmaf(dscQ, fmaf(ri, cQ, -rr * sQ), yQ);
+                    // Re(conj r' i (X_P - X_Q)) / r
+                    G0 = fmaf(fmaf(ri, XPr - XQr, -rr * (XPi - XQi)), a.rinv, G0);
+                }
+            }
+            // per-direction results: sum_r rho_0, sum_r rho_i r, sum_r rho_1 r, sum_r rho_2 r
+            const float ya = -(g1d + g2d) * (1.0f / 3.0f);
+            const float yb = (2.0f * g1d - g2d) * (1.0f / 3.0f);
+            const float yc = (2.0f * g2d - g1d) * (1.0f / 3.0f);
+            const float dq1 = (-yb * yc + 2.0f * ya * yc - ya * yb) * (1.0f / 3.0f);
+            const float dq2 = (-yb * yc - ya * yc + 2.0f * ya * yb) * (1.0f / 3.0f);
+            double T0 = 0.5 * (double)S0h + (double)S0t;
+            double Ti = (0.5 * (double)Sih + (double)Sit) * (1.0 / 3.0);
+            double T1 = (double)yb * SA + (double)dq1 * SB;
+            double T2 = (double)yc * SA + (double)dq2 * SB;
+            if (xP != 0.0f || yP != 0.0f || xQ != 0.0f || yQ != 0.0f || G0 != 0.0f) {
+                const float g3d = g2d - g1d;
+                const float a1 = fabsf(g1d), a2 = fabsf(g2d), a3 = fabsf(g3d);
+                const bool caseA = (a2 >= a1) && (a2 >= a3);
+                const bool caseB = !caseA && (a1 >= a3);
+                float oP1, oP2, hP1, hP2, oQ1, oQ2, hQ1, hQ2, D0, D1, D2;
+                if (caseA) {
+                    oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
+                    oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
+                    D0 = g2d; D1 = 0.0f; D2 = 1.0f;
+                } else if (caseB) {
+                    oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
+                    oQ1 = -1.0f / 3; oQ2 = 1.0f / 6; hQ1 = 0.0f; hQ2 = 0.5f;
+                    D0 = g1d; D1 = 1.0f; D2 = 0.0f;
+                } else {
+                    oP1 = -1.0f / 3; oP2 = 1.0f / 6; hP1 = 0.0f; hP2 = 0.5f;
+                    oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
+                    D0 = g3d; D1 = -1.0f; D2 = 1.0f;
+                }
+                const double iD = 1.0 / (double)D0;
+                T0 += (double)G0 * iD;
+                Ti += ((double)xP - (double)xQ) * iD * (1.0 / 3.0);
+                T1 += ((double)oP1 * xP + (double)hP1 * yP - (double)oQ1 * xQ - (double)hQ1 * yQ) * iD -
+                      (double)D1 * G0 * iD * iD;
+                T2 += ((double)oP2 * xP + (double)hP2 * yP - (double)oQ2 * xQ - (double)hQ2 * yQ) * iD -
+                      (double)D2 * G0 * iD * iD;
+            }
+            const double wx = dir[d], wy = dir[n_dir + d], wz = dir[2 * n_dir + d];
+            acc[0][threadIdx.x] += T0;
+            acc[1][threadIdx.x] += wx * Ti;
+            acc[2][threadIdx.x] += wy * Ti;
+            acc[3][threadIdx.x] += wz * Ti;
+            acc[4][threadIdx.x] += wx * T1;
+            acc[5][threadIdx.x] += wy * T1;
+            acc[6][threadIdx.x] += wz * T1;
+            acc[7][threadIdx.x] += wx * T2;
+            acc[8][threadIdx.x] += wy * T2;
+            acc[9][threadIdx.x] += wz * T2;
+        }
+        if (active) {
+            double* o = partial + ((int64_t)chunk * nt + tri) * 10;
+            for (int c = 0; c < 10; ++c) o[c] = acc[c][threadIdx.x];
+        }
+    }
+}
+
 // Sum the node chunks per triangle (fixed order), apply d gamma/dp_j and gamma,
 // and store the three corner contributions. Each (vertex, component) records
 // the largest binary exponent among its contributions, and each vertex its
@@ -591,15 +871,17 @@ __global__ void adjoint_scatter(const double* __restrict__ corner, const int32_t
     }
 }
 
-int resident_adjoint(wd_ctx* ctx, int precision)
+int resident_adjoint(wd_ctx* ctx, int precision, bool radial = false)
 {
-    static int cached[2][64] = {{0}};
-    const int m = precision == WD_MIXED ? 1 : 0;
+    static int cached[3][64] = {{0}};
+    const int m = radial ? 2 : (precision == WD_MIXED ? 1 : 0);
     int& c = cached[m][ctx->device & 63];
     if (c == 0) {
         int per_sm = 0;
-        cudaError_t e = m ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_mixed, ADJ_TPB, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_f64, ADJ_TPB, 0);
+        cudaError_t e =
+            m == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_radial, ADJ_TPB, 0)
+            : m == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_mixed, ADJ_TPB, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_f64, ADJ_TPB, 0);
         if (e != cudaSuccess || per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
@@ -634,19 +916,63 @@ wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n
     return WD_OK;
 }
 
+wd_status wd_plan_adjoint_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int64_t n_tris, AdjPlan* plan)
+{
+    if (precision != WD_MIXED || !rule->d_rad || rule->n_rad > ADJ_RMAX || rule->n_dir <= 0)
+        return wd_plan_adjoint(ctx, precision, rule->n_eval, n_tris, plan);
+    AdjPlan p;
+    p.radial = true;
+    p.n_tb = (n_tris + ADJ_TPB - 1) / ADJ_TPB;
+    const int64_t resident = resident_adjoint(ctx, precision, true);
+    const int64_t target = 4 * resident;
+    int64_t nchunks = 1;
+    if (p.n_tb > 0 && p.n_tb < target) nchunks = (target + p.n_tb - 1) / p.n_tb;
+    if (nchunks > rule->n_dir) nchunks = rule->n_dir;
+    p.dirs_per_chunk = (rule->n_dir + nchunks - 1) / nchunks;
+    p.nchunks = (int)((rule->n_dir + p.dirs_per_chunk - 1) / p.dirs_per_chunk);
+    p.n_items = p.n_tb * p.nchunks;
+    p.grid = (int)(p.n_items < resident ? p.n_items : resident);
+    *plan = p;
+    return WD_OK;
+}
+
+size_t wd_adjoint_radial_bytes(const wd_rule* rule)
+{
+    return sizeof(float4) * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1);
+}
+
 size_t wd_adjoint_scatter_bytes(int64_t nt, int64_t nv)
 {
     const size_t corner = ((sizeof(double) * 9 * (size_t)(nt > 0 ? nt : 1)) + 255) & ~size_t(255);
     return corner + sizeof(int) * 4 * (size_t)(nv > 0 ? nv : 1);
 }
 
-wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
+wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const wd_rule* rule,
                             const double* d_resid, const void* d_rec, const void* d_rec_mixed, int64_t nt,
-                            double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv, double* d_grad,
-                            cudaStream_t st)
+                            void* d_radial, double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv,
+                            double* d_grad, cudaStream_t st)
 {
     if (nt == 0) return WD_OK;
-    if (plan.n_items > 0) {
+    const double* d_xi = rule->d_xi;
+    const int64_t n = rule->n_eval;
+    if (plan.radial && plan.n_items > 0) {
+        if (precision != WD_MIXED || !rule->d_rad || !d_radial) {
+            wd_set_error("internal: radial adjoint plan without a mixed ball rule");
+            return WD_EINVAL;
+        }
+        float4* nd = static_cast<float4*>(d_radial);
+        int64_t g = (n + 255) / 256;
+        const int64_t cap = (int64_t)ctx->num_sms * 8;
+        if (g > cap) g = cap;
+        adjoint_prep_radial<<<(int)g, 256, 0, st>>>(d_resid, rule->n_rad, rule->n_dir, nd);
+        ctx->launches++;
+        WD_CUDA(cudaGetLastError());
+        adjoint_kernel_radial<<<plan.grid, ADJ_TPB, 0, st>>>(static_cast<const TriRecF*>(d_rec_mixed), nt, nd,
+                                                            rule->d_rad, rule->n_rad, rule->d_dir, rule->n_dir,
+                                                            plan, d_partial);
+        ctx->launches++;
+        WD_CUDA(cudaGetLastError());
+    } else if (plan.n_items > 0) {
         if (precision == WD_MIXED)
             adjoint_kernel_mixed<<<plan.grid, ADJ_TPB, 0, st>>>(d_xi, n, d_resid,
                                                                static_cast<const TriRecF*>(d_rec_mixed), nt, plan,

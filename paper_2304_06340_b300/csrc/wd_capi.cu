@@ -407,7 +407,7 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     const int64_t n = rule->n_eval;
     CoreLayout L = core_layout(ctx, rule, precision, MODE_RESID, nt + nt2, base);
     AdjPlan ap;
-    wd_plan_adjoint(ctx, precision, n, nt, &ap);
+    wd_plan_adjoint_rule(ctx, rule, precision, nt, &ap);
     size_t off = L.end;
     const size_t o_res = off;
     off += align_up(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
@@ -417,6 +417,8 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     off += align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) * (size_t)(nt > 0 ? nt : 1));
     const size_t o_sc = off;
     off += align_up(wd_adjoint_scatter_bytes(nt, nv));
+    const size_t o_rad = off;
+    if (ap.radial) off += align_up(wd_adjoint_radial_bytes(rule));
     wd_status st_ = wd_ws_reserve(ctx, off);
     if (st_ != WD_OK) return st_;
     if ((st_ = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st_;
@@ -452,9 +454,9 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     // adjoint over mu's triangles, staged in float64
     void* rec64 = ctx->ws + o_rec64;
     if ((st_ = wd_launch_stage(ctx, WD_FP64, d_verts, nv, d_tris, nt, 1.0, rec64, 0, st)) != WD_OK) return st_;
-    return wd_launch_adjoint(ctx, precision, ap, rule->d_xi, n, resid, rec64, precision == WD_MIXED ? rec : nullptr,
-                             nt, reinterpret_cast<double*>(ctx->ws + o_adj), ctx->ws + o_sc, d_tris, nv, d_grad,
-                             st);
+    return wd_launch_adjoint(ctx, precision, ap, rule, resid, rec64, precision == WD_MIXED ? rec : nullptr, nt,
+                             ap.radial ? ctx->ws + o_rad : nullptr, reinterpret_cast<double*>(ctx->ws + o_adj),
+                             ctx->ws + o_sc, d_tris, nv, d_grad, st);
 }
 
 extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
@@ -506,12 +508,13 @@ extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const 
         const int64_t nt2 = m2 ? m2->n_tris : 0;
         CoreLayout L = core_layout(ctx, rule, precision, MODE_RESID, mu->n_tris + nt2, base);
         AdjPlan ap;
-        wd_plan_adjoint(ctx, precision, rule->n_eval, mu->n_tris, &ap);
+        wd_plan_adjoint_rule(ctx, rule, precision, mu->n_tris, &ap);
         size_t need = L.end + align_up(sizeof(double) * 2 * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1)) +
                       align_up(sizeof(TriRecD) * (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
                       align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) *
                                (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
-                      align_up(wd_adjoint_scatter_bytes(mu->n_tris, mu->n_verts));
+                      align_up(wd_adjoint_scatter_bytes(mu->n_tris, mu->n_verts)) +
+                      (ap.radial ? align_up(wd_adjoint_radial_bytes(rule)) : 0);
         if ((st = wd_ws_reserve(ctx, need)) != WD_OK) return st;
     }
     if ((st = upload_mesh(ctx, mu, ov, ot, strm)) != WD_OK) return st;

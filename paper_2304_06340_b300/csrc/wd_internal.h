@@ -165,6 +165,8 @@ wd_status wd_launch_sphere(wd_ctx* ctx, const double* d_xi, int64_t n, double ra
                            cudaStream_t st);
 // adjoint (wd_adjoint.cu): gradient of D with respect to the vertices of mu
 struct AdjPlan {
+    bool radial = false;     // radial mixed adjoint: chunks are ranges of directions
+    int64_t dirs_per_chunk = 0;
     int64_t n_tb = 0;        // triangle blocks
     int64_t n_node_tiles = 0;
     int tiles_per_chunk = 0;
@@ -173,15 +175,20 @@ struct AdjPlan {
     int grid = 0;
 };
 wd_status wd_plan_adjoint(wd_ctx* ctx, int precision, int64_t n_nodes, int64_t n_tris, AdjPlan* plan);
+// plan for a rule: the radial adjoint for ball rules in the mixed path, else as above
+wd_status wd_plan_adjoint_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int64_t n_tris, AdjPlan* plan);
+// scratch of the radial adjoint (the rotated residual, direction-major)
+size_t wd_adjoint_radial_bytes(const wd_rule* rule);
 // d_rec: float64 records of mu (geometry for the final scatter, and the
 // float64 adjoint); d_rec_mixed: mixed records of mu (mixed adjoint);
 // d_scatter: wd_adjoint_scatter_bytes(nt, nv) bytes of scratch. d_grad must
 // be zeroed by the caller; the result is bitwise independent of launch order.
 size_t wd_adjoint_scatter_bytes(int64_t nt, int64_t nv);
-wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const double* d_xi, int64_t n,
+// d_radial: wd_adjoint_radial_bytes(rule) bytes when plan.radial, else unused
+wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, const wd_rule* rule,
                             const double* d_resid, const void* d_rec, const void* d_rec_mixed, int64_t nt,
-                            double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv, double* d_grad,
-                            cudaStream_t st);
+                            void* d_radial, double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv,
+                            double* d_grad, cudaStream_t st);
 
 // batched serving kernel (wd_pair.cu), driven by a device descriptor table
 struct ServeReq {

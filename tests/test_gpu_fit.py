@@ -1,7 +1,8 @@
 """Adjoint configuration on the GPU: bitwise-reproducible gradients, the
 gradient of a 5,120-triangle jittered mesh against the oracle on a sampled
-sub-rule of the 1,179,648-node ball rule, and the gradient-descent fit toward
-the unit sphere with checkpoint/resume."""
+explicit sub-rule of the 1,179,648-node ball rule (per-node adjoint) and on a
+ball rule with the same 192 radii (radial adjoint), and the gradient-descent
+fit toward the unit sphere with checkpoint/resume."""
 import numpy as np
 import pytest
 
@@ -58,6 +59,24 @@ def test_adjoint_config_gradient_vs_oracle(ctx):
     xs, ws = np.ascontiguousarray(xo[::96]), np.ascontiguousarray(wo[::96])
     d_or, g_or = oracle.distance_grad(xs, ws, 1.0, v, t)
     rule = ctx.rule_from_nodes(xs, ws)
+    dv, dt = _dev(v, t)
+    for prec, tol in ((wd.WD_FP64, 1e-10), (wd.WD_MIXED, 1e-6)):
+        d, g = _grad(ctx, rule, dv, dt, prec)
+        g = g.cpu().numpy()
+        assert abs(d.item() - d_or) < tol * d_or
+        err = np.linalg.norm(g - g_or) / np.linalg.norm(g_or)
+        assert err < tol, (prec, err)
+
+
+def test_adjoint_config_radial_gradient_vs_oracle(ctx):
+    # the radial (ball-rule) mixed adjoint over the adjoint rule's full radial
+    # range: R=128 with its 192 radii, on 2 x 6 directions (2,304 nodes),
+    # n=16 mesh, sigma=0.01, seed 3
+    v, t = synth.adjoint_mesh(16, 3)
+    desc = (128.0, 192, 4, 6, True)
+    xo, wo = oracle.ball_rule(*desc)
+    d_or, g_or = oracle.distance_grad(xo, wo, 1.0, v, t)
+    rule = ctx.rule(*desc)
     dv, dt = _dev(v, t)
     for prec, tol in ((wd.WD_FP64, 1e-10), (wd.WD_MIXED, 1e-6)):
         d, g = _grad(ctx, rule, dv, dt, prec)
