@@ -42,11 +42,13 @@ def lib():
         L.or_ball_rule.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, _dp, _dp]
         L.or_ball_rule.restype = _i64
+        L.or_cube_rule.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.or_cube_rule.restype = _i64
         L.or_triangle_ft.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
         L.or_divided_difference.argtypes = [_dp, ctypes.c_int, _dp, _dp]
         L.or_mesh_ft.argtypes = [_dp, _i64, _ip, _i64, _dp, _i64, _dp, _dp, ctypes.c_int]
         L.or_sphere_ft.argtypes = [_dp, _i64, ctypes.c_double, _dp, _dp, _dp]
-        dist_args = [_dp, _dp, _i64, ctypes.c_double, _dp, _i64, _ip, _i64, ctypes.c_int,
+        dist_args = [_dp, _dp, _i64, ctypes.c_double, ctypes.c_double, _dp, _i64, _ip, _i64, ctypes.c_int,
                      ctypes.c_double, _dp, _dp, _i64, _ip, _i64]
         L.or_distance.argtypes = dist_args + [_dp, _dp, ctypes.c_int]
         L.or_distance.restype = ctypes.c_double
@@ -87,6 +89,22 @@ def ball_rule(R, n_r, n_polar, n_azim, hermitian):
     xi = np.empty((n, 3))
     w = np.empty(n)
     lib().or_ball_rule(R, n_r, n_polar, n_azim, int(bool(hermitian)), _d(xi)[1], _d(w)[1])
+    return xi, w
+
+
+# weight scale of the paper's convention: (1 + |eta|^2) = (1 + |xi|^2 / (4 pi^2)) at xi = 2 pi eta
+PAPER_WSCALE = 1.0 / (4.0 * np.pi ** 2)
+
+
+def cube_rule(xmax, M, hermitian):
+    """Nodes (N, 3), angular xi = 2 pi eta, and weights (N,) of the paper's cube
+    trapezoid rule on [-xmax, xmax]^3 in eta (oracle's own build)."""
+    n = lib().or_cube_rule(xmax, M, int(bool(hermitian)), None, None)
+    if n < 0:
+        raise ValueError("invalid cube rule")
+    xi = np.empty((n, 3))
+    w = np.empty(n)
+    lib().or_cube_rule(xmax, M, int(bool(hermitian)), _d(xi)[1], _d(w)[1])
     return xi, w
 
 
@@ -144,8 +162,8 @@ def _nu_args(nu):
     return (1, 0.0, (None, None), v2, len(v2[0]), t2, len(t2[0]))
 
 
-def distance(xi, w_geom, s, verts, tris, nu=None, nthreads=None, return_mu=False):
-    """D = sum_k w_k (1+|xi_k|^2)^-s |mu^(xi_k) - nu^(xi_k)|^2 (long double)."""
+def distance(xi, w_geom, s, verts, tris, nu=None, nthreads=None, return_mu=False, wscale=1.0):
+    """D = sum_k w_k (1 + wscale |xi_k|^2)^-s |mu^(xi_k) - nu^(xi_k)|^2 (long double)."""
     x, xp = _d(xi)
     w, wp = _d(w_geom)
     v, vp = _d(verts)
@@ -153,7 +171,7 @@ def distance(xi, w_geom, s, verts, tris, nu=None, nthreads=None, return_mu=False
     kind, radius, c, v2, nv2, t2, nt2 = _nu_args(nu)
     mu_re = np.empty(len(x)) if return_mu else None
     mu_im = np.empty(len(x)) if return_mu else None
-    d = lib().or_distance(xp, wp, len(x), float(s), vp, len(v), tp, len(t), kind, radius, c[1],
+    d = lib().or_distance(xp, wp, len(x), float(s), float(wscale), vp, len(v), tp, len(t), kind, radius, c[1],
                           v2[1], nv2, t2[1], nt2,
                           _d(mu_re)[1] if return_mu else None,
                           _d(mu_im)[1] if return_mu else None,
@@ -165,14 +183,14 @@ def distance(xi, w_geom, s, verts, tris, nu=None, nthreads=None, return_mu=False
     return d
 
 
-def distance_grad(xi, w_geom, s, verts, tris, nu=None, nthreads=None):
+def distance_grad(xi, w_geom, s, verts, tris, nu=None, nthreads=None, wscale=1.0):
     x, xp = _d(xi)
     w, wp = _d(w_geom)
     v, vp = _d(verts)
     t, tp = _i(tris)
     kind, radius, c, v2, nv2, t2, nt2 = _nu_args(nu)
     g = np.empty((len(v), 3))
-    d = lib().or_distance_grad(xp, wp, len(x), float(s), vp, len(v), tp, len(t), kind, radius,
+    d = lib().or_distance_grad(xp, wp, len(x), float(s), float(wscale), vp, len(v), tp, len(t), kind, radius,
                                c[1], v2[1], nv2, t2[1], nt2, _d(g)[1],
                                nthreads or default_threads())
     if np.isnan(d):

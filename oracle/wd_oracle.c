@@ -17,6 +17,9 @@
  * which is the ball-truncated quadrature of the Plancherel form of the squared
  * Sobolev norm, Eq. (sobolev_2), with order -s and no (2 pi)^-3 factor.
  *
+ * or_cube_rule gives the paper's own lattice rule in its 2 pi convention; the
+ * weighted sums take a weight scale for it (see weight_ld).
+ *
  * Parity status of every function is stated in its comment; the pins live in
  * tests/test_oracle_pins.py.
  */
@@ -71,6 +74,45 @@ int or_gauss_legendre(int n, double* x_out, double* w_out)
         w_out[n - i] = (double)(2.0L / ((1.0L - x * x) * dp * dp));
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cube trapezoid rule of the paper's experiments (Sec. 3.2, the lattice of
+ * Eq. (def_trap_grid) with the three-dimensional trapezoidal rule of Eq.
+ * (trap_rule_R3)), in the paper's 2 pi convention: eta_{ijk} = (i, j, k) h,
+ * h = 2 xmax / M, i, j, k = -M/2 .. M/2, weight h^3 times 1/2 per coordinate
+ * on the boundary (1 inside, 1/2 on faces, 1/4 on edges, 1/8 at corners).
+ * The nodes are returned in the angular convention, xi = 2 pi eta, so that
+ * mu^(xi) is the paper's transform at eta; the paper's weight
+ * (1 + |eta|^2)^(-s) is (1 + wscale |xi|^2)^(-s) with wscale = 1/(4 pi^2).
+ * With `hermitian`, the half eta_z > 0, or eta_z = 0 and eta_y > 0, or
+ * eta_z = eta_y = 0 and eta_x >= 0 is kept, every node but the origin with
+ * doubled weight. Node order: k outermost, then j, then i (fastest).
+ * Returns the node count, or -1 on invalid arguments (M even, >= 2). */
+int64_t or_cube_rule(double xmax, int M, int hermitian, double* xi, double* w_geom)
+{
+    if (!(xmax > 0.0) || M < 2 || (M % 2)) return -1;
+    const int m = M / 2;
+    const ld h = 2.0L * (ld)xmax / (ld)M;
+    int64_t cnt = 0;
+    for (int k = hermitian ? 0 : -m; k <= m; ++k)
+        for (int j = -m; j <= m; ++j)
+            for (int i = -m; i <= m; ++i) {
+                if (hermitian && (k == 0) && (j < 0 || (j == 0 && i < 0))) continue;
+                if (xi) {
+                    const ld fi = (i == m || i == -m) ? 0.5L : 1.0L;
+                    const ld fj = (j == m || j == -m) ? 0.5L : 1.0L;
+                    const ld fk = (k == m || k == -m) ? 0.5L : 1.0L;
+                    const int origin = (i == 0 && j == 0 && k == 0);
+                    const ld dup = (hermitian && !origin) ? 2.0L : 1.0L;
+                    xi[3 * cnt] = (double)(2.0L * OR_PI * h * i);
+                    xi[3 * cnt + 1] = (double)(2.0L * OR_PI * h * j);
+                    xi[3 * cnt + 2] = (double)(2.0L * OR_PI * h * k);
+                    w_geom[cnt] = (double)(h * h * h * fi * fj * fk * dup);
+                }
+                ++cnt;
+            }
+    return cnt;
 }
 
 /* ------------------------------------------------------------------ */
@@ -362,14 +404,16 @@ static void nu_ft_ld(const nu_desc* nu, const double* xi, ld* re, ld* im)
     else mesh_ft_node_ld(nu->verts, nu->tris, nu->nt, xi, re, im);
 }
 
-static ld weight_ld(const double* xi, double w_geom, double s)
+/* W = w (1 + wscale |xi|^2)^(-s): wscale = 1 in the angular convention, and
+ * 1/(4 pi^2) for the paper's (1 + |eta|^2)^(-s) at xi = 2 pi eta. */
+static ld weight_ld(const double* xi, double w_geom, double s, double wscale)
 {
-    return (ld)w_geom * powl(1.0L + dotl(xi, xi), -(ld)s);
+    return (ld)w_geom * powl(1.0L + (ld)wscale * dotl(xi, xi), -(ld)s);
 }
 
 /* D = sum_k W_k |mu^ - nu^|^2 over explicit nodes (Eq. (sobolev_2) as a
  * quadrature sum). Optional per-node outputs of mu^ (may be NULL). */
-double or_distance(const double* xi, const double* w_geom, int64_t n, double s,
+double or_distance(const double* xi, const double* w_geom, int64_t n, double s, double wscale,
                    const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                    int nu_kind, double radius, const double* center,
                    const double* verts2, int64_t nv2, const int32_t* tris2, int64_t nt2,
@@ -385,7 +429,7 @@ double or_distance(const double* xi, const double* w_geom, int64_t n, double s,
         mesh_ft_node_ld(verts, tris, nt, xi + 3 * k, &mr, &mi);
         nu_ft_ld(&nu, xi + 3 * k, &vr, &vi);
         ld dr = mr - vr, di = mi - vi;
-        term[k] = weight_ld(xi + 3 * k, w_geom[k], s) * (dr * dr + di * di);
+        term[k] = weight_ld(xi + 3 * k, w_geom[k], s, wscale) * (dr * dr + di * di);
         if (mu_re) mu_re[k] = (double)mr;
         if (mu_im) mu_im[k] = (double)mi;
     }
@@ -403,7 +447,7 @@ double or_distance(const double* xi, const double* w_geom, int64_t n, double s,
  * n the unit normal of (b - a) x (c - a); the derivative of a divided
  * difference in one node is the divided difference with that node repeated.
  * A degenerate triangle (gamma = 0) contributes zero. grad is nv x 3. */
-double or_distance_grad(const double* xi, const double* w_geom, int64_t n, double s,
+double or_distance_grad(const double* xi, const double* w_geom, int64_t n, double s, double wscale,
                         const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                         int nu_kind, double radius, const double* center,
                         const double* verts2, int64_t nv2, const int32_t* tris2, int64_t nt2,
@@ -420,7 +464,7 @@ double or_distance_grad(const double* xi, const double* w_geom, int64_t n, doubl
         ld mr, mi, vr, vi;
         mesh_ft_node_ld(verts, tris, nt, xi + 3 * k, &mr, &mi);
         nu_ft_ld(&nu, xi + 3 * k, &vr, &vi);
-        ld w = weight_ld(xi + 3 * k, w_geom[k], s);
+        ld w = weight_ld(xi + 3 * k, w_geom[k], s, wscale);
         ld dr = mr - vr, di = mi - vi;
         term[k] = w * (dr * dr + di * di);
         res_r[k] = 2.0L * w * dr;

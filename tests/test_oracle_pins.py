@@ -296,6 +296,59 @@ def test_sphere_norm_closed_form():
 
 
 # ----------------------------------------------------------------- meshes
+@pytest.mark.parametrize("herm", [False, True])
+def test_cube_rule_is_the_product_trapezoid(herm):
+    # Sec. 3.2, Eqs. (def_trap_grid), (trap_rule_R3): the 3-D trapezoidal rule
+    # on [-xmax, xmax]^3 is the product of 1-D trapezoidal rules, so on a
+    # separable (even, for the Hermitian half) integrand it equals the product
+    # of numpy's 1-D trapezoid sums; nodes are 2 pi times the lattice.
+    xmax, M = 1.3, 6
+    xi, w = oracle.cube_rule(xmax, M, herm)
+    n_full = (M + 1) ** 3
+    assert len(xi) == ((n_full + 1) // 2 if herm else n_full)
+    eta = xi / (2 * np.pi)
+    grid = np.linspace(-xmax, xmax, M + 1)
+    assert np.allclose(np.sort(np.unique(np.round(eta[:, 0], 12))), grid, atol=1e-12)
+    fa = lambda x: np.cos(1.7 * x) + x ** 2  # noqa: E731
+    fb = lambda y: np.exp(-0.6 * y ** 2)  # noqa: E731
+    fc = lambda z: np.cosh(0.9 * z)  # noqa: E731
+    lhs = np.sum(w * fa(eta[:, 0]) * fb(eta[:, 1]) * fc(eta[:, 2]))
+    rhs = np.trapezoid(fa(grid), grid) * np.trapezoid(fb(grid), grid) * np.trapezoid(fc(grid), grid)
+    assert lhs == pytest.approx(rhs, rel=1e-14)
+    assert np.sum(w) == pytest.approx((2 * xmax) ** 3, rel=1e-14)
+    if not herm:  # odd factors integrate to zero on the symmetric lattice
+        assert abs(np.sum(w * eta[:, 0] * fb(eta[:, 1]))) < 1e-14
+
+
+def test_cube_rule_sphere_norm_as_the_paper_reports():
+    # Sec. 4.1 (Fig. 3b): with xmax = 5 the cube trapezoidal rule for the
+    # unit sphere's H_s norm, against the closed form Eq.
+    # (sphere_sobolev_exact), is limited by truncation at about 1e-7 for
+    # s = -5, while for s = -10 it keeps converging to round-off; the paper's
+    # convention is the weight (1 + |eta|^2)^s at xi = 2 pi eta.
+    empty_v, empty_t = np.zeros((0, 3)), np.zeros((0, 3), dtype=np.int32)
+    sphere = ("sphere", 1.0, (0.0, 0.0, 0.0))
+
+    def rel_err(M, s_p):
+        xi, w = oracle.cube_rule(5.0, M, True)
+        cf = 4 * math.pi ** 1.5 / sp.gamma(-s_p) * (
+            sp.gamma(-s_p - 0.5) - 2 * (2 * math.pi) ** (-s_p - 0.5) * sp.kv(-s_p - 0.5, 4 * math.pi))
+        d = oracle.distance(xi, w, -s_p, empty_v, empty_t, nu=sphere, wscale=oracle.PAPER_WSCALE)
+        return abs(d - cf) / cf
+
+    e5_64, e5_128 = rel_err(64, -5.0), rel_err(128, -5.0)
+    assert 1e-8 < e5_64 < 1e-7 and 1e-8 < e5_128 < 1e-7          # truncation plateau
+    assert abs(e5_128 - e5_64) < 0.05 * e5_64
+    assert rel_err(32, -10.0) > 1e-3 and rel_err(64, -10.0) < 1e-6  # fast convergence
+    assert rel_err(128, -10.0) < 1e-12
+    # the Hermitian half equals the full lattice
+    xf, wf = oracle.cube_rule(5.0, 32, False)
+    xh, wh = oracle.cube_rule(5.0, 32, True)
+    df = oracle.distance(xf, wf, 10.0, empty_v, empty_t, nu=sphere, wscale=oracle.PAPER_WSCALE)
+    dh = oracle.distance(xh, wh, 10.0, empty_v, empty_t, nu=sphere, wscale=oracle.PAPER_WSCALE)
+    assert dh == pytest.approx(df, rel=1e-14)
+
+
 def test_icosahedral_counts_and_total_area():
     for N in range(0, 5):
         v, t = synth.icosphere(2 ** N)
