@@ -60,7 +60,7 @@ typedef enum {
 } wd_status;
 
 enum { WD_FP64 = 0, WD_MIXED = 1 };               /* arithmetic of the pair kernel */
-enum { WD_RULE_BALL = 0, WD_RULE_EXPLICIT = 2 };  /* frequency-rule kinds */
+enum { WD_RULE_BALL = 0, WD_RULE_CUBE_TRAP = 1, WD_RULE_EXPLICIT = 2 };  /* frequency-rule kinds */
 enum { WD_NU_SPHERE = 0, WD_NU_MESH = 1 };        /* reference-measure kinds */
 
 typedef struct wd_ctx wd_ctx;
@@ -93,12 +93,26 @@ wd_status wd_sync(wd_ctx* ctx, void* stream);
  * hermitian != 0 keeps only u > 0 and doubles its weight, which is exact for
  * real measures because |mu^ - nu^|^2 is even in xi (n_polar must be even).
  * Node order: r outermost, then u ascending, then phi fastest. */
+/* WD_RULE_CUBE_TRAP is the rule of the paper's own experiments (Sec. 3.2:
+ * the lattice of Eq. (def_trap_grid) with the trapezoidal rule of Eq.
+ * (trap_rule_R3)), in the paper's 2 pi convention (Eq. (ft_measure)):
+ *   eta_{ijk} = (i, j, k) h,  h = 2 R / n_r,  i, j, k = -n_r/2 .. n_r/2,
+ *   weight h^3 x (1/2 per coordinate on the boundary of [-R, R]^3),
+ * with R = xi_max in the paper's frequency units and n_r = M (even, >= 2);
+ * n_polar and n_azim are ignored. The rule's nodes are stored in this
+ * library's angular convention, xi = 2 pi eta, so mu^(xi) is the paper's
+ * transform at eta, and its per-call weight is the paper's
+ * (1 + |eta|^2)^(-s) = (1 + |xi|^2 / (4 pi^2))^(-s): with this kind, D is the
+ * paper's squared H_{-s} norm of mu - nu, Eq. (sobolev_2), quadrature of
+ * Eq. (trap_rule_R3). hermitian != 0 keeps the half eta_z > 0, or eta_z = 0
+ * and eta_y > 0, or eta_z = eta_y = 0 and eta_x >= 0, doubling every weight
+ * but the origin's. Node order: eta_z outermost, then eta_y, eta_x fastest. */
 typedef struct {
-    int kind;      /* WD_RULE_BALL */
-    double R;      /* truncation radius, > 0 */
-    int n_r;       /* radial nodes, >= 1 */
-    int n_polar;   /* polar nodes, >= 1 (even when hermitian) */
-    int n_azim;    /* azimuthal nodes, >= 1 */
+    int kind;      /* WD_RULE_BALL or WD_RULE_CUBE_TRAP */
+    double R;      /* ball: truncation radius; cube: xi_max (paper units); > 0 */
+    int n_r;       /* ball: radial nodes, >= 1; cube: M, even, >= 2 */
+    int n_polar;   /* ball: polar nodes, >= 1 (even when hermitian) */
+    int n_azim;    /* ball: azimuthal nodes, >= 1 */
     int hermitian; /* 0 or 1 */
 } wd_rule_desc;
 

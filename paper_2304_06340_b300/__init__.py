@@ -17,7 +17,7 @@ from . import _build
 
 WD_OK, WD_EINVAL, WD_ENOMEM, WD_ECUDA, WD_EBUSY, WD_ETIMEOUT, WD_ENOTFOUND, WD_ECANCELLED = range(8)
 WD_FP64, WD_MIXED = 0, 1
-WD_RULE_BALL, WD_RULE_EXPLICIT = 0, 2
+WD_RULE_BALL, WD_RULE_CUBE_TRAP, WD_RULE_EXPLICIT = 0, 1, 2
 WD_NU_SPHERE, WD_NU_MESH = 0, 1
 STATUS_NAMES = {0: "WD_OK", 1: "WD_EINVAL", 2: "WD_ENOMEM", 3: "WD_ECUDA", 4: "WD_EBUSY",
                 5: "WD_ETIMEOUT", 6: "WD_ENOTFOUND", 7: "WD_ECANCELLED"}
@@ -184,11 +184,19 @@ def wd_sync(ctx, stream=None):
     _check(_lib.wd_sync(ctx, _stream(stream)))
 
 
-def wd_build_freq_rule(ctx, R, n_r, n_polar, n_azim, hermitian=False):
-    d = wd_rule_desc(WD_RULE_BALL, float(R), int(n_r), int(n_polar), int(n_azim), int(bool(hermitian)))
+def wd_build_freq_rule(ctx, R, n_r, n_polar, n_azim, hermitian=False, kind=WD_RULE_BALL):
+    """kind WD_RULE_BALL: (R, n_r, n_polar, n_azim); kind WD_RULE_CUBE_TRAP:
+    R = xi_max and n_r = M of the paper's cube trapezoid rule (n_polar and
+    n_azim ignored)."""
+    d = wd_rule_desc(int(kind), float(R), int(n_r), int(n_polar), int(n_azim), int(bool(hermitian)))
     h = _vp()
     _check(_lib.wd_build_freq_rule(ctx, ctypes.byref(d), ctypes.byref(h)))
     return h
+
+
+def wd_build_cube_rule(ctx, xi_max, M, hermitian=True):
+    """The paper's cube trapezoid rule (see WD_RULE_CUBE_TRAP in include/wd.h)."""
+    return wd_build_freq_rule(ctx, xi_max, M, 0, 0, hermitian, kind=WD_RULE_CUBE_TRAP)
 
 
 def wd_rule_from_nodes(ctx, xi, w_geom):
@@ -379,6 +387,9 @@ class Context:
 
     def rule(self, R, n_r, n_polar, n_azim, hermitian=False):
         return wd_build_freq_rule(self.handle, R, n_r, n_polar, n_azim, hermitian)
+
+    def cube_rule(self, xi_max, M, hermitian=True):
+        return wd_build_cube_rule(self.handle, xi_max, M, hermitian)
 
     def rule_from_nodes(self, xi, w_geom):
         return wd_rule_from_nodes(self.handle, xi, w_geom)

@@ -63,6 +63,7 @@ struct wd_rule {
     std::vector<float> h_dir;         // ball rules: directions, layout of d_dir
     double* d_xi = nullptr;           // SoA on the device
     double* d_wg = nullptr;
+    double wscale = 1.0;              // W = w (1 + wscale |xi|^2)^(-s); 1/(4 pi^2) for cube rules
     // ball rules only: node k = rad[k / n_dir] * omega[k % n_dir] (radius outer)
     int n_rad = 0;
     int64_t n_dir = 0;
@@ -225,4 +226,4 @@ wd_status wd_launch_serve(wd_ctx* ctx, int precision, int grid, const ServeTable
 int wd_serve_resident(wd_ctx* ctx, int precision);
 
 wd_status wd_launch_weights(wd_ctx* ctx, const double* d_xi, const double* d_wg, int64_t n,
-                            double s, double* d_w, cudaStream_t st);
+                            double s, double wscale, double* d_w, cudaStream_t st);

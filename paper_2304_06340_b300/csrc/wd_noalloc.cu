@@ -116,7 +116,7 @@ extern "C" wd_status wd_distance_dev_noalloc(const double* d_xi, const double* d
 
     double* W = reinterpret_cast<double*>(base + o_w);
     double* nu = reinterpret_cast<double*>(base + o_nu);
-    if ((st = wd_launch_weights(ctx, d_xi, d_w_geom, n_nodes, s, W, strm)) != WD_OK) return st;
+    if ((st = wd_launch_weights(ctx, d_xi, d_w_geom, n_nodes, s, 1.0, W, strm)) != WD_OK) return st;
     if ((st = wd_launch_sphere(ctx, d_xi, n_nodes, radius, center, nullptr, nullptr, nu, strm)) != WD_OK)
         return st;
     void* rec = base + o_rec;

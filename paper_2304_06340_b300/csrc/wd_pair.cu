@@ -330,6 +330,25 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     return s;  // valid in warp 0
 }
 
+// mu^(0) = sum_T gamma_T / 2 exactly: the float64 sum, in fixed order, of the
+// records' float-pair gamma, returned to every thread of the block. Used for a
+// node at the origin in the mixed path: there every pair has the same phase,
+// so the float32 roundings of the pairs repeat for congruent triangles and add
+// up instead of averaging out, while the origin carries a full weight in
+// lattice rules.
+__device__ __noinline__ double origin_transform(const TriRecF* __restrict__ rec, int64_t T, double* red)
+{
+    double v = 0.0;
+    for (int64_t j = threadIdx.x; j < T; j += blockDim.x) v += (double)rec[j].gam + (double)rec[j].gam_lo;
+    const double s = block_sum(v, red);
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = s;
+    __syncthreads();
+    const double tot = red[0];
+    __syncthreads();
+    return 0.5 * tot;
+}
+
 // Per-node end of one work item, called by every thread of the block: combine
 // the triangle chunks of the node block in fixed order (the last chunk to
 // finish does it), undo the mixed path's phase dither, then write mu^ (FT) or
@@ -371,6 +390,15 @@ __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan&
         const double r_ = mr * cd + mi * sd;
         mi = mi * cd - mr * sd;
         mr = r_;
+        // a node at the origin takes the exact total (block-uniform branch)
+        const bool origin = active && a.xi[node] == 0.0 && a.xi[n + node] == 0.0 && a.xi[2 * n + node] == 0.0;
+        if (__syncthreads_or(origin)) {
+            const double m0 = origin_transform(static_cast<const TriRecF*>(a.tris), a.T, red);
+            if (origin) {
+                mr = m0;
+                mi = 0.0;
+            }
+        }
     }
 
     if (MODE == MODE_FT) {
@@ -956,6 +984,14 @@ __global__ void __launch_bounds__(WD_NPB, 4) serve_kernel(const ServeTable* __re
             const double r_ = mr * cd + mi * sd;
             mi = mi * cd - mr * sd;
             mr = r_;
+            const bool origin = active && x == 0.0 && y == 0.0 && z == 0.0;
+            if (__syncthreads_or(origin)) {
+                const double m0 = origin_transform(static_cast<const TriRecF*>(rq.rec), rq.T, red);
+                if (origin) {
+                    mr = m0;
+                    mi = 0.0;
+                }
+            }
         }
         double term = 0.0;
         if (active) {

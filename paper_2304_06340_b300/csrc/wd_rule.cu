@@ -61,13 +61,13 @@ void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w)
 }
 
 __global__ void weights_kernel(const double* __restrict__ xi, const double* __restrict__ wg,
-                               int64_t n, double s, double* __restrict__ w)
+                               int64_t n, double s, double wscale, double* __restrict__ w)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         double x = xi[k], y = xi[n + k], z = xi[2 * n + k];
         double r2 = fma(x, x, fma(y, y, z * z));
-        w[k] = wg[k] * exp(-s * log1p(r2));
+        w[k] = wg[k] * exp(-s * log1p(wscale * r2));
     }
 }
 
@@ -150,10 +150,10 @@ bool same_desc(const wd_rule_desc& a, const wd_rule_desc& b)
 }  // namespace
 
 wd_status wd_launch_weights(wd_ctx* ctx, const double* d_xi, const double* d_wg, int64_t n,
-                            double s, double* d_w, cudaStream_t st)
+                            double s, double wscale, double* d_w, cudaStream_t st)
 {
     if (n == 0) return WD_OK;
-    weights_kernel<<<grid_for(ctx, n), 256, 0, st>>>(d_xi, d_wg, n, s, d_w);
+    weights_kernel<<<grid_for(ctx, n), 256, 0, st>>>(d_xi, d_wg, n, s, wscale, d_w);
     ctx->launches++;
     WD_CUDA(cudaGetLastError());
     return WD_OK;
@@ -186,7 +186,7 @@ wd_status wd_rule_weights(wd_ctx* ctx, wd_rule* rule, double s, const double** d
         wd_set_error("out of device memory for rule weights");
         return WD_ENOMEM;
     }
-    wd_status stt = wd_launch_weights(ctx, rule->d_xi, rule->d_wg, rule->n_eval, s, w, st);
+    wd_status stt = wd_launch_weights(ctx, rule->d_xi, rule->d_wg, rule->n_eval, s, rule->wscale, w, st);
     if (stt != WD_OK) {
         cudaFree(w);
         return stt;
@@ -225,10 +225,69 @@ wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double
 }
 
 // ------------------------------------------------------------------ C ABI
+// The paper's cube trapezoid rule (Sec. 3.2), nodes at xi = 2 pi eta: see
+// WD_RULE_CUBE_TRAP in wd.h. Built in long double like the ball rule.
+static wd_status build_cube_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** out)
+{
+    WD_CHECK(std::isfinite(d->R) && d->R > 0.0, WD_EINVAL, "xi_max must be finite and > 0");
+    WD_CHECK(d->n_r >= 2 && d->n_r % 2 == 0, WD_EINVAL, "cube rule: M (n_r) must be even and >= 2");
+    const int64_t side = (int64_t)d->n_r + 1;
+    const int64_t n_total = side * side * side;
+    WD_CHECK(n_total <= (int64_t)1 << 31, WD_EINVAL, "rule too large (more than 2^31 nodes)");
+    wd_rule_desc key = *d;
+    key.n_polar = key.n_azim = 0;
+    key.hermitian = d->hermitian ? 1 : 0;
+    wd_status st = wd_activate(ctx);
+    if (st != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    for (wd_rule* r : ctx->rules)
+        if (same_desc(r->desc, key)) {
+            *out = r;
+            return WD_OK;
+        }
+    const int m = d->n_r / 2;
+    const bool herm = key.hermitian != 0;
+    wd_rule* r = new wd_rule();
+    r->desc = key;
+    r->cached = true;
+    r->n_total = n_total;
+    r->n_eval = herm ? (n_total + 1) / 2 : n_total;
+    r->wscale = 1.0 / (4.0 * (double)(kPi * kPi));
+    const int64_t n = r->n_eval;
+    r->h_xi.resize(3 * n);
+    r->h_wg.resize(n);
+    const long double h = 2.0L * (long double)d->R / (long double)d->n_r;
+    const long double tpih = 2.0L * kPi * h;
+    int64_t k = 0;
+    for (int iz = herm ? 0 : -m; iz <= m; ++iz)
+        for (int iy = -m; iy <= m; ++iy)
+            for (int ix = -m; ix <= m; ++ix) {
+                if (herm && iz == 0 && (iy < 0 || (iy == 0 && ix < 0))) continue;
+                const long double fx = (ix == m || ix == -m) ? 0.5L : 1.0L;
+                const long double fy = (iy == m || iy == -m) ? 0.5L : 1.0L;
+                const long double fz = (iz == m || iz == -m) ? 0.5L : 1.0L;
+                const bool origin = ix == 0 && iy == 0 && iz == 0;
+                r->h_xi[k] = (double)(tpih * ix);
+                r->h_xi[n + k] = (double)(tpih * iy);
+                r->h_xi[2 * n + k] = (double)(tpih * iz);
+                r->h_wg[k] = (double)(h * h * h * fx * fy * fz * ((herm && !origin) ? 2.0L : 1.0L));
+                ++k;
+            }
+    st = upload_rule(ctx, r);
+    if (st != WD_OK) {
+        release_rule(r);
+        return st;
+    }
+    ctx->rules.push_back(r);
+    *out = r;
+    return WD_OK;
+}
+
 extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** out)
 {
     WD_CHECK(ctx && d && out, WD_EINVAL, "null argument");
-    WD_CHECK(d->kind == WD_RULE_BALL, WD_EINVAL, "only WD_RULE_BALL descriptors are built");
+    if (d->kind == WD_RULE_CUBE_TRAP) return build_cube_rule(ctx, d, out);
+    WD_CHECK(d->kind == WD_RULE_BALL, WD_EINVAL, "rule kind must be WD_RULE_BALL or WD_RULE_CUBE_TRAP");
     WD_CHECK(std::isfinite(d->R) && d->R > 0.0, WD_EINVAL, "R must be finite and > 0");
     WD_CHECK(d->n_r >= 1 && d->n_polar >= 1 && d->n_azim >= 1, WD_EINVAL, "node counts must be >= 1");
     WD_CHECK(!d->hermitian || d->n_polar % 2 == 0, WD_EINVAL,

@@ -236,6 +236,14 @@ ADJOINT_NS = (16, 32)
 ADJOINT_SIGMA = 0.01
 ADJOINT_SEEDS = tuple(range(64))
 
+# the paper's own experiment (Sec. 4.2, Fig. 4b): icosahedral T_N, N = 0..7,
+# against the unit sphere in H_{-10} on the cube trapezoid rule xi_max = 5,
+# M = 128 (paper's 2 pi convention); this library's order s = 10
+PAPER_XI_MAX = 5.0
+PAPER_M = 128
+PAPER_S = 10.0
+PAPER_LEVELS = tuple(range(8))
+
 # serving stream rules keyed by truncation radius
 SERVE_RULES = {64.0: BallRule(64.0, 64, 32, 64, True), 128.0: BallRule(128.0, 128, 48, 96, True)}
 

@@ -1,0 +1,115 @@
+"""The paper's own experiment on the GPU: the cube trapezoid rule in the
+paper's 2 pi convention (Sec. 3.2), the unit sphere's H_{-s} norm against its
+closed form, icosahedral T_N against the oracle, and the O(4^-N) convergence
+of Fig. 4b reaching about 1e-5 at N = 7 (Sec. 4.2)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2304_06340_b300 as wd  # noqa: E402
+
+EMPTY_V, EMPTY_T = np.zeros((0, 3)), np.zeros((0, 3), dtype=np.int32)
+SPHERE = ("sphere", 1.0, (0.0, 0.0, 0.0))
+
+
+def sphere_norm2(s):
+    """Eq. (sphere_sobolev_exact) with the paper's order s_p = -s."""
+    sp_ = -s
+    return 4 * math.pi ** 1.5 / sp.gamma(-sp_) * (
+        sp.gamma(-sp_ - 0.5) - 2 * (2 * math.pi) ** (-sp_ - 0.5) * sp.kv(-sp_ - 0.5, 4 * math.pi))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = wd.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("herm", [False, True])
+def test_cube_rule_nodes_match_oracle(ctx, herm):
+    rule = ctx.cube_rule(5.0, 16, herm)
+    n_eval, n_total = wd.wd_rule_info(rule)
+    assert n_total == 17 ** 3
+    xi, w = wd.wd_rule_copy_nodes(rule)
+    xo, wo = oracle.cube_rule(5.0, 16, herm)
+    assert n_eval == len(xo)
+    assert np.allclose(xi, xo, rtol=0, atol=1e-13) and np.allclose(w, wo, rtol=1e-15, atol=0)
+
+
+def test_cube_rule_rejects_bad_descriptors(ctx):
+    for xmax, M in ((5.0, 15), (5.0, 0), (0.0, 16), (float("nan"), 16)):
+        with pytest.raises(wd.WDError):
+            ctx.cube_rule(xmax, M, True)
+
+
+@pytest.mark.parametrize("prec", [wd.WD_FP64, wd.WD_MIXED])
+def test_sphere_norm_on_the_paper_rule(ctx, prec):
+    # no triangles: D = sum W |sigma^|^2, the rule's value of the sphere's
+    # squared norm, converged to round-off for s = -10 at M = 128 (Fig. 3b)
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    d = ctx.distance(rule, EMPTY_V, EMPTY_T, None, synth.PAPER_S, prec)
+    assert d == pytest.approx(sphere_norm2(synth.PAPER_S), rel=1e-12)
+
+
+def test_mixed_transform_at_the_origin_is_the_exact_area(ctx):
+    # every pair has the same phase at xi = 0, so the mixed path takes the
+    # float64 total of the triangles' gamma / 2 there (a lattice node)
+    v, t = synth.icosphere_recursive(3)
+    v = synth.jitter_isotropic(v, 0.01, 4)
+    xi = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1]])
+    ref = oracle.mesh_ft(v, t, xi)
+    rule = ctx.rule_from_nodes(xi, np.ones(2))
+    mu = wd.wd_mesh_ft(ctx.handle, rule, v, t, wd.WD_MIXED)
+    assert abs(mu[0] - ref[0]) <= 1e-15 * abs(ref[0])
+    assert abs(mu[1] - ref[1]) <= 1e-6 * abs(ref[0])
+    cube = ctx.cube_rule(5.0, 8, True)  # its first node is the origin
+    mu = wd.wd_mesh_ft(ctx.handle, cube, v, t, wd.WD_MIXED)
+    assert abs(mu[0] - ref[0]) <= 1e-15 * abs(ref[0])
+
+
+@pytest.mark.parametrize("N", [0, 1, 2])
+def test_paper_rule_distance_matches_oracle(ctx, N):
+    v, t = synth.icosphere_recursive(N)
+    xo, wo = oracle.cube_rule(synth.PAPER_XI_MAX, 32, True)
+    d_or = oracle.distance(xo, wo, synth.PAPER_S, v, t, wscale=oracle.PAPER_WSCALE)
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, 32, True)
+    d64 = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_FP64)
+    dmx = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_MIXED)
+    assert d64 == pytest.approx(d_or, rel=1e-12)
+    assert dmx == pytest.approx(d_or, rel=1e-6)
+
+
+def test_paper_fig4b_convergence(ctx):
+    # Sec. 4.2: relative H_{-10} error of T_N, xi_max = 5, M = 128, parallel to
+    # O(4^-N) and at the level of 1e-5 for N = 7
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    norm = math.sqrt(sphere_norm2(synth.PAPER_S))
+    err = []
+    for N in synth.PAPER_LEVELS:
+        v, t = synth.icosphere_recursive(N)
+        d = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_MIXED)
+        err.append(math.sqrt(d) / norm)
+    ratios = [a / b for a, b in zip(err[1:], err[2:])]
+    assert all(3.5 < q < 4.5 for q in ratios), (err, ratios)
+    assert 3e-6 < err[7] < 3e-5, err
+
+
+def test_paper_rule_mixed_matches_fp64_at_N5(ctx):
+    # the mixed path on the paper's rule where D / |mu|^2 is ~1e-9
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    v, t = synth.icosphere_recursive(5)
+    d64 = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_FP64)
+    dmx = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_MIXED)
+    assert dmx == pytest.approx(d64, rel=1e-6)
