@@ -137,11 +137,16 @@ wd_status upload_mesh(wd_ctx* ctx, const wd_mesh* m, size_t ov, size_t ot, cudaS
 }  // namespace
 
 // ------------------------------------------------------------------ internals
-void wd_set_error(const std::string& msg) { g_last_error = msg; }
+void wd_set_error(const std::string& msg)
+{
+    g_last_error = msg;
+    wd_log(1, "%s", msg.c_str());
+}
 
 wd_status wd_cuda_status(cudaError_t e, const char* what)
 {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    wd_log(1, "%s", g_last_error.c_str());
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return WD_ENOMEM;
@@ -163,7 +168,7 @@ wd_status wd_ws_reserve(wd_ctx* ctx, size_t bytes)
     cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
-    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    if (wd_dev_alloc(&ctx->ws, want, "context scratch") != cudaSuccess) {
         cudaGetLastError();
         ctx->ws = nullptr;
         wd_set_error("out of device memory for scratch (" + std::to_string(want) + " bytes)");
@@ -181,7 +186,7 @@ wd_status wd_counters_reserve(wd_ctx* ctx, int64_t n)
     cudaFree(ctx->d_counters);
     ctx->d_counters = nullptr;
     ctx->n_counters = 0;
-    if (cudaMalloc(&ctx->d_counters, sizeof(int) * want) != cudaSuccess) {
+    if (wd_dev_alloc(&ctx->d_counters, sizeof(int) * want, "completion counters") != cudaSuccess) {
         cudaGetLastError();
         wd_set_error("out of device memory for completion counters");
         return WD_ENOMEM;
@@ -205,9 +210,9 @@ extern "C" wd_status wd_create(int device, wd_ctx** out)
     wd_ctx* c = new wd_ctx();
     c->device = device;
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = wd_dev_alloc(&c->d_flags, 4 * sizeof(int), "context flags");
     if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, 4 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_scalar, 4 * sizeof(double));
+    if (e == cudaSuccess) e = wd_dev_alloc(&c->d_scalar, 4 * sizeof(double), "context scalars");
     if (e != cudaSuccess) {
         wd_status st = wd_cuda_status(e, "wd_create");
         cudaFree(c->d_flags);
@@ -215,6 +220,7 @@ extern "C" wd_status wd_create(int device, wd_ctx** out)
         delete c;
         return st;
     }
+    wd_log(3, "context created on device %d (%d SMs)", device, c->num_sms);
     *out = c;
     return WD_OK;
 }
@@ -247,6 +253,7 @@ extern "C" wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule_c, const do
                                     int64_t nv, const int32_t* d_tris, int64_t nt, int precision,
                                     double* d_re, double* d_im, void* stream)
 {
+    WdRange nvtx_range("wd_mesh_ft_dev");
     wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
     WD_CHECK(nv >= 0 && nt >= 0 && nt <= ((int64_t)1 << 31), WD_EINVAL, "mesh size out of range");
@@ -265,6 +272,7 @@ extern "C" wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule_c, const do
 extern "C" wd_status wd_mesh_ft(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mesh, int precision,
                                 double* out_re, double* out_im)
 {
+    WdRange nvtx_range("wd_mesh_ft");
     wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
     std::string why;
@@ -298,6 +306,7 @@ extern "C" wd_status wd_mesh_ft(wd_ctx* ctx, const wd_rule* rule_c, const wd_mes
 extern "C" wd_status wd_sphere_ft_dev(wd_ctx* ctx, const wd_rule* rule, double radius, const double center[3],
                                       double* d_re, double* d_im, void* stream)
 {
+    WdRange nvtx_range("wd_sphere_ft_dev");
     wd_status st = check_common(ctx, rule, WD_FP64);
     if (st != WD_OK) return st;
     WD_CHECK(center, WD_EINVAL, "null center");
@@ -312,6 +321,7 @@ extern "C" wd_status wd_sphere_ft_dev(wd_ctx* ctx, const wd_rule* rule, double r
 extern "C" wd_status wd_sphere_ft(wd_ctx* ctx, const wd_rule* rule, double radius, const double center[3],
                                   double* out_re, double* out_im)
 {
+    WdRange nvtx_range("wd_sphere_ft");
     wd_status st = check_common(ctx, rule, WD_FP64);
     if (st != WD_OK) return st;
     const int64_t n = rule->n_eval;
@@ -335,6 +345,7 @@ extern "C" wd_status wd_distance_dev(wd_ctx* ctx, const wd_rule* rule_c, const d
                                      int64_t nv, const int32_t* d_tris, int64_t nt, const wd_measure* nu,
                                      double s, int precision, double* d_dist2, void* stream)
 {
+    WdRange nvtx_range("wd_distance_dev");
     wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
     if ((st = check_nu(nu)) != WD_OK) return st;
@@ -356,6 +367,7 @@ extern "C" wd_status wd_distance_dev(wd_ctx* ctx, const wd_rule* rule_c, const d
 extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mu, const wd_measure* nu,
                                  double s, int precision, double* dist2)
 {
+    WdRange nvtx_range("wd_distance");
     wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
     if ((st = check_nu(nu)) != WD_OK) return st;
@@ -463,6 +475,7 @@ extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, co
                                           int64_t nv, const int32_t* d_tris, int64_t nt, const wd_measure* nu,
                                           double s, int precision, double* d_dist2, double* d_grad, void* stream)
 {
+    WdRange nvtx_range("wd_distance_grad_dev");
     wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
     if ((st = check_nu(nu)) != WD_OK) return st;
@@ -481,6 +494,7 @@ extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, co
 extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mu, const wd_measure* nu,
                                       double s, int precision, double* dist2, double* grad_verts)
 {
+    WdRange nvtx_range("wd_distance_grad");
     wd_status st = check_common(ctx, rule_c, precision);
     if (st != WD_OK) return st;
     if ((st = check_nu(nu)) != WD_OK) return st;

@@ -13,6 +13,27 @@
 
 #include "wd.h"
 
+// ------------------------------------------------------------------ runtime support (wd_runtime.cu)
+int wd_log_level();
+void wd_log(int level, const char* fmt, ...);  // 1 error, 2 warn, 3 info, 4 debug (stderr, WD_LOG)
+// device allocation: honours WD_FAULT_ALLOC and WD_POISON_SCRATCH
+cudaError_t wd_dev_alloc(void** p, size_t bytes, const char* what);
+template <typename T>
+cudaError_t wd_dev_alloc(T** p, size_t bytes, const char* what)
+{
+    void* q = nullptr;
+    cudaError_t e = wd_dev_alloc(&q, bytes, what);
+    *p = static_cast<T*>(q);
+    return e;
+}
+int wd_fault_drop_completion();  // WD_FAULT_DROP_COMPLETION (0: off)
+
+// NVTX range for the duration of a scope (shows in Nsight timelines)
+struct WdRange {
+    explicit WdRange(const char* name);
+    ~WdRange();
+};
+
 // ------------------------------------------------------------------ errors
 void wd_set_error(const std::string& msg);
 wd_status wd_cuda_status(cudaError_t e, const char* what);

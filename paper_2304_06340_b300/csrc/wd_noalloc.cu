@@ -63,6 +63,7 @@ extern "C" wd_status wd_distance_dev_noalloc(const double* d_xi, const double* d
                                              int64_t n_tris, double s, double radius, const double center[3],
                                              int precision, double* d_dist2, void* stream)
 {
+    WdRange nvtx_range("wd_distance_dev_noalloc");
     WD_CHECK(precision == WD_FP64 || precision == WD_MIXED, WD_EINVAL, "precision must be WD_FP64 or WD_MIXED");
     WD_CHECK(std::isfinite(s) && s > 0.0, WD_EINVAL, "s must be finite and > 0");
     WD_CHECK(std::isfinite(radius) && radius > 0.0, WD_EINVAL, "sphere radius must be finite and > 0");

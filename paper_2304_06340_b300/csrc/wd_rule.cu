@@ -103,14 +103,14 @@ wd_status upload_rule(wd_ctx* ctx, wd_rule* r)
 {
     const int64_t n = r->n_eval;
     if (n > 0) {
-        WD_CUDA(cudaMalloc(&r->d_xi, sizeof(double) * 3 * n));
-        WD_CUDA(cudaMalloc(&r->d_wg, sizeof(double) * n));
+        WD_CUDA(wd_dev_alloc(&r->d_xi, sizeof(double) * 3 * n, "rule nodes"));
+        WD_CUDA(wd_dev_alloc(&r->d_wg, sizeof(double) * n, "rule weights"));
         WD_CUDA(cudaMemcpy(r->d_xi, r->h_xi.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
         WD_CUDA(cudaMemcpy(r->d_wg, r->h_wg.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     }
     if (!r->h_rad.empty()) {
-        WD_CUDA(cudaMalloc(&r->d_rad, sizeof(double) * r->h_rad.size()));
-        WD_CUDA(cudaMalloc(&r->d_dir, sizeof(float) * r->h_dir.size()));
+        WD_CUDA(wd_dev_alloc(&r->d_rad, sizeof(double) * r->h_rad.size(), "rule radii"));
+        WD_CUDA(wd_dev_alloc(&r->d_dir, sizeof(float) * r->h_dir.size(), "rule directions"));
         WD_CUDA(cudaMemcpy(r->d_rad, r->h_rad.data(), sizeof(double) * r->h_rad.size(), cudaMemcpyHostToDevice));
         WD_CUDA(cudaMemcpy(r->d_dir, r->h_dir.data(), sizeof(float) * r->h_dir.size(), cudaMemcpyHostToDevice));
     }
@@ -180,7 +180,7 @@ wd_status wd_rule_weights(wd_ctx* ctx, wd_rule* rule, double s, const double** d
         return WD_OK;
     }
     double* w = nullptr;
-    cudaError_t e = cudaMalloc(&w, sizeof(double) * (rule->n_eval > 0 ? rule->n_eval : 1));
+    cudaError_t e = wd_dev_alloc(&w, sizeof(double) * (rule->n_eval > 0 ? rule->n_eval : 1), "weights cache");
     if (e != cudaSuccess) {
         cudaGetLastError();
         wd_set_error("out of device memory for rule weights");
@@ -207,7 +207,7 @@ wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double
         return WD_OK;
     }
     double* nu = nullptr;
-    cudaError_t e = cudaMalloc(&nu, sizeof(double) * 2 * (rule->n_eval > 0 ? rule->n_eval : 1));
+    cudaError_t e = wd_dev_alloc(&nu, sizeof(double) * 2 * (rule->n_eval > 0 ? rule->n_eval : 1), "sphere cache");
     if (e != cudaSuccess) {
         cudaGetLastError();
         wd_set_error("out of device memory for the cached sphere transform");
@@ -279,12 +279,14 @@ static wd_status build_cube_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** o
         return st;
     }
     ctx->rules.push_back(r);
+    wd_log(3, "cube rule xi_max=%g M=%d hermitian=%d: %lld nodes", d->R, d->n_r, key.hermitian, (long long)n);
     *out = r;
     return WD_OK;
 }
 
 extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** out)
 {
+    WdRange nvtx_range("wd_build_freq_rule");
     WD_CHECK(ctx && d && out, WD_EINVAL, "null argument");
     if (d->kind == WD_RULE_CUBE_TRAP) return build_cube_rule(ctx, d, out);
     WD_CHECK(d->kind == WD_RULE_BALL, WD_EINVAL, "rule kind must be WD_RULE_BALL or WD_RULE_CUBE_TRAP");

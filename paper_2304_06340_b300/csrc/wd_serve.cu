@@ -33,7 +33,9 @@ constexpr int kRoundRobinBlocks = 8;  // node blocks taken per request per round
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-enum ReqState { PENDING = 0, ADMITTED = 1, DONE = 2, FAILED = 3 };
+// LOST: finished, but its completion dropped by WD_FAULT_DROP_COMPLETION, so
+// the client never sees it done (its waits run out)
+enum ReqState { PENDING = 0, ADMITTED = 1, DONE = 2, FAILED = 3, LOST = 4 };
 
 struct Request {
     uint64_t ticket = 0;
@@ -138,6 +140,8 @@ struct wd_server {
     bool any_submit = false;
     double busy_s = 0.0;
     wd_status fatal = WD_OK;
+    int drop_nth = 0;        // WD_FAULT_DROP_COMPLETION at start (0: off)
+    int64_t n_ok_seen = 0;   // successful completions so far
 };
 
 namespace {
@@ -153,6 +157,15 @@ size_t request_bytes(const wd_server* sv, const Request* r)
 
 void finish(wd_server* sv, Request* r, wd_status status, double result)
 {
+    if (status == WD_OK && sv->drop_nth > 0 && ++sv->n_ok_seen == sv->drop_nth) {
+        // injected fault: the work is done but the completion never reaches the client
+        wd_log(2, "injected fault: completion of ticket %llu dropped", (unsigned long long)r->ticket);
+        r->state = LOST;
+        r->verts.clear();
+        r->tris.clear();
+        sv->st.completed++;
+        return;
+    }
     r->state = status == WD_OK ? DONE : FAILED;
     r->status = status;
     r->result = result;
@@ -374,6 +387,7 @@ void worker_main(wd_server* sv)
         }
         if (n_items == 0 && finishing.empty()) continue;
         const auto t0 = Clock::now();
+        WdRange nvtx_range("wd_serve launch");
         cudaError_t e = cudaGraphLaunch(sv->graph, sv->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
         const auto t1 = Clock::now();
@@ -441,7 +455,7 @@ extern "C" wd_status wd_serve_start(wd_ctx* ctx, const wd_serve_config* cfg, wd_
     }
     if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(wd_cuda_status(cudaGetLastError(), "cudaStreamCreate"));
-    if (cudaMalloc(&sv->d_arena, (size_t)cfg->mem_cap_bytes) != cudaSuccess) {
+    if (wd_dev_alloc(&sv->d_arena, (size_t)cfg->mem_cap_bytes, "serving arena") != cudaSuccess) {
         cudaGetLastError();
         wd_set_error("cannot allocate the serving arena");
         return fail(WD_ENOMEM);
@@ -453,8 +467,8 @@ extern "C" wd_status wd_serve_start(wd_ctx* ctx, const wd_serve_config* cfg, wd_
     sv->table_bytes = sv->off_fin + align_up(sizeof(ServeFin) * kMaxSlots);
     if (cudaHostAlloc(&sv->h_table, sv->table_bytes, cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc(&sv->h_results, sizeof(double) * kMaxSlots, cudaHostAllocDefault) != cudaSuccess ||
-        cudaMalloc(&sv->d_table, sv->table_bytes) != cudaSuccess ||
-        cudaMalloc(&sv->d_results, sizeof(double) * kMaxSlots) != cudaSuccess) {
+        wd_dev_alloc(&sv->d_table, sv->table_bytes, "serving table") != cudaSuccess ||
+        wd_dev_alloc(&sv->d_results, sizeof(double) * kMaxSlots, "serving results") != cudaSuccess) {
         cudaGetLastError();
         wd_set_error("cannot allocate the serving tables");
         return fail(WD_ENOMEM);
@@ -462,6 +476,9 @@ extern "C" wd_status wd_serve_start(wd_ctx* ctx, const wd_serve_config* cfg, wd_
     std::memset(sv->h_table, 0, sv->table_bytes);
     sv->grid = wd_serve_resident(ctx, cfg->precision);
     if ((st = capture_graph(sv)) != WD_OK) return fail(st);
+    sv->drop_nth = wd_fault_drop_completion();
+    wd_log(3, "server started: %d slots, arena %lld bytes, %d rules, grid %d", cfg->max_slots,
+           (long long)cfg->mem_cap_bytes, cfg->n_rules, sv->grid);
     sv->worker = std::thread(worker_main, sv);
     *out = sv;
     return WD_OK;
