@@ -163,9 +163,13 @@ struct PairArgs {
 
 constexpr int WD_NPB = 256;   // nodes per block: one node per thread
 constexpr int WD_TILE = 128;  // triangles per shared-memory tile
-constexpr int WD_RAD_NR = 64;                   // radial plan: radii per block (two warps per direction)
-constexpr int WD_RAD_ND = WD_NPB / WD_RAD_NR;   // radial plan: directions per block
-constexpr int WD_RAD_TILE = 64;                 // radial plan: triangles per record tile
+// radial plan (ball rules, mixed path): a block covers WD_RAD_ND directions x
+// WD_RAD_NR radii; each thread takes WD_RAD_RPT radii of one direction
+constexpr int WD_RAD_RPT = 1;  // radii per thread; 2 ran slower (381 vs 407 Gpair/s on the n=64 sweep query)
+constexpr int WD_RAD_NR = 64;                        // radii per block
+constexpr int WD_RAD_TPD = WD_RAD_NR / WD_RAD_RPT;   // threads per direction
+constexpr int WD_RAD_ND = WD_NPB / WD_RAD_TPD;       // directions per block
+constexpr int WD_RAD_TILE = WD_NPB / WD_RAD_ND;      // triangles per record tile (one record per thread)
 
 size_t wd_tri_record_bytes(int precision);
 // stage triangles (a1): records for mu (sign +1) at offset 0 and optionally a

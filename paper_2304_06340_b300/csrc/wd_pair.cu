@@ -349,80 +349,102 @@ __device__ __noinline__ double origin_transform(const TriRecF* __restrict__ rec,
     return 0.5 * tot;
 }
 
-// Per-node end of one work item, called by every thread of the block: combine
-// the triangle chunks of the node block in fixed order (the last chunk to
-// finish does it), undo the mixed path's phase dither, then write mu^ (FT) or
-// subtract nu^, weight, write the residual (RESID) and reduce D in fixed order
-// (the last node block to finish adds the block sums).
-template <bool MIXED, int MODE>
+// Per-node end of one work item, called by every thread of the block with its
+// K nodes: combine the triangle chunks of the node block in fixed order (the
+// last chunk to finish does it), undo the mixed path's phase dither, then
+// write mu^ (FT) or subtract nu^, weight, write the residual (RESID) and reduce
+// D in fixed order (the last node block to finish adds the block sums).
+template <bool MIXED, int MODE, int K>
 __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan& p, int64_t nb, int chunk,
-                                              int64_t node, bool active, float dith, double acc_r, double acc_i,
-                                              double* red, int& s_last)
+                                              const int64_t* node, const bool* active, const float* dith,
+                                              const double* acc_r, const double* acc_i, double* red, int& s_last)
 {
     const int64_t n = a.n;
+    double mr[K], mi[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        mr[q] = acc_r[q];
+        mi[q] = acc_i[q];
+    }
     // ---- combine triangle chunks of this node block (fixed order)
-    double mr = acc_r, mi = acc_i;
     if (p.nchunks > 1) {
-        if (active) {
-            a.partial[2 * ((int64_t)chunk * n + node)] = acc_r;
-            a.partial[2 * ((int64_t)chunk * n + node) + 1] = acc_i;
-        }
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if (active[q]) {
+                a.partial[2 * ((int64_t)chunk * n + node[q])] = acc_r[q];
+                a.partial[2 * ((int64_t)chunk * n + node[q]) + 1] = acc_i[q];
+            }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) s_last = (atomicAdd(&a.cnt[nb], 1) == p.nchunks - 1);
         __syncthreads();
         if (!s_last) return;
         __threadfence();
-        mr = 0.0;
-        mi = 0.0;
-        if (active)
-            for (int c = 0; c < p.nchunks; ++c) {
-                mr += __ldcg(&a.partial[2 * ((int64_t)c * n + node)]);
-                mi += __ldcg(&a.partial[2 * ((int64_t)c * n + node) + 1]);
-            }
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            mr[q] = 0.0;
+            mi[q] = 0.0;
+            if (active[q])
+                for (int c = 0; c < p.nchunks; ++c) {
+                    mr[q] += __ldcg(&a.partial[2 * ((int64_t)c * n + node[q])]);
+                    mi[q] += __ldcg(&a.partial[2 * ((int64_t)c * n + node[q]) + 1]);
+                }
+        }
         if (threadIdx.x == 0) a.cnt[nb] = 0;  // ready for the next launch
     }
 
     if (MIXED) {
-        // undo the phase dither: mu^ = S exp(-2 pi i dith), in float64
-        double sd, cd;
-        sincospi(2.0 * (double)dith, &sd, &cd);
-        const double r_ = mr * cd + mi * sd;
-        mi = mi * cd - mr * sd;
-        mr = r_;
+        bool origin[K], any = false;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            // undo the phase dither: mu^ = S exp(-2 pi i dith), in float64
+            double sd, cd;
+            sincospi(2.0 * (double)dith[q], &sd, &cd);
+            const double r_ = mr[q] * cd + mi[q] * sd;
+            mi[q] = mi[q] * cd - mr[q] * sd;
+            mr[q] = r_;
+            origin[q] = active[q] && a.xi[node[q]] == 0.0 && a.xi[n + node[q]] == 0.0 &&
+                        a.xi[2 * n + node[q]] == 0.0;
+            any = any || origin[q];
+        }
         // a node at the origin takes the exact total (block-uniform branch)
-        const bool origin = active && a.xi[node] == 0.0 && a.xi[n + node] == 0.0 && a.xi[2 * n + node] == 0.0;
-        if (__syncthreads_or(origin)) {
+        if (__syncthreads_or(any)) {
             const double m0 = origin_transform(static_cast<const TriRecF*>(a.tris), a.T, red);
-            if (origin) {
-                mr = m0;
-                mi = 0.0;
-            }
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (origin[q]) {
+                    mr[q] = m0;
+                    mi[q] = 0.0;
+                }
         }
     }
 
     if (MODE == MODE_FT) {
-        if (active) {
-            a.out[node] = mr;
-            a.out_im[node] = mi;
-        }
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if (active[q]) {
+                a.out[node[q]] = mr[q];
+                a.out_im[node[q]] = mi[q];
+            }
         return;
     }
 
     // ---- distance epilogue (a6, a7): subtract nu^, weight, reduce
     double term = 0.0;
-    if (active) {
-        double dr = mr, di = mi;
-        if (a.nu) {
-            dr -= a.nu[2 * node];
-            di -= a.nu[2 * node + 1];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        if (active[q]) {
+            double dr = mr[q], di = mi[q];
+            if (a.nu) {
+                dr -= a.nu[2 * node[q]];
+                di -= a.nu[2 * node[q] + 1];
+            }
+            term += a.W[node[q]] * (dr * dr + di * di);
+            if (MODE == MODE_RESID) {
+                a.resid[2 * node[q]] = 2.0 * a.W[node[q]] * dr;
+                a.resid[2 * node[q] + 1] = 2.0 * a.W[node[q]] * di;
+            }
         }
-        term = a.W[node] * (dr * dr + di * di);
-        if (MODE == MODE_RESID) {
-            a.resid[2 * node] = 2.0 * a.W[node] * dr;
-            a.resid[2 * node + 1] = 2.0 * a.W[node] * di;
-        }
-    }
     const double bsum = block_sum(term, red);
     if (threadIdx.x == 0) {
         a.blockD[nb] = bsum;
@@ -526,8 +548,8 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
             }
         }
 
-        node_epilogue<MIXED, MODE>(a, p, nb, chunk, node, active, MIXED ? qf.dith : 0.0f, acc_r, acc_i, red,
-                                   s_last);
+        const float dith = MIXED ? qf.dith : 0.0f;
+        node_epilogue<MIXED, MODE, 1>(a, p, nb, chunk, &node, &active, &dith, &acc_r, &acc_i, red, s_last);
     }
 }
 
@@ -669,55 +691,83 @@ __device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__
     fi = fmaf(g2, s, fmaf(g2, ti, l2 * s));
 }
 
-// One thread's node in a radial node block: block nb covers directions
-// [dg WD_RAD_ND, +WD_RAD_ND) x radii [rg WD_RAD_NR, +WD_RAD_NR); thread t
-// takes direction t / WD_RAD_NR (warp-uniform) and radius t % WD_RAD_NR.
+// One thread's nodes in a radial node block: block nb covers directions
+// [dg WD_RAD_ND, +WD_RAD_ND) x radii [rg WD_RAD_NR, +WD_RAD_NR); thread t takes
+// direction t / WD_RAD_TPD (warp-uniform) and the WD_RAD_RPT radii
+// t % WD_RAD_TPD + q WD_RAD_TPD, q < WD_RAD_RPT, of the block's radius group.
 struct RadThread {
-    int64_t dg, node;
+    int64_t dg;
     int dl;
-    bool dir_ok, active;
-    float rh, rlo;   // radius as a float pair
-    float rho, r3;   // r^2, r^3
-    float thr;       // Taylor branch while gmax0 < thr = DELTA / r
-    float rinv;      // 1 / r
-    float dith;      // the node's phase dither
+    bool dir_ok;
+    int64_t node[WD_RAD_RPT];
+    bool active[WD_RAD_RPT];
+    float rh[WD_RAD_RPT], rlo[WD_RAD_RPT];   // radius as a float pair
+    float rho[WD_RAD_RPT], r3[WD_RAD_RPT];   // r^2, r^3
+    float thr[WD_RAD_RPT];                   // Taylor branch while gmax0 < thr = DELTA / r
+    float rinv[WD_RAD_RPT];                  // 1 / r
+    float dith[WD_RAD_RPT];                  // the node's phase dither
 };
 
 __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ rad, int n_rad, int64_t n_dir,
                                                    int64_t nb, int n_rg)
 {
     RadThread h;
-    h.dl = threadIdx.x / WD_RAD_NR;
-    const int rl = threadIdx.x % WD_RAD_NR;
+    h.dl = threadIdx.x / WD_RAD_TPD;
+    const int rl = threadIdx.x % WD_RAD_TPD;
     h.dg = nb / n_rg;
     const int rg = (int)(nb - h.dg * n_rg);
     const int64_t d = h.dg * WD_RAD_ND + h.dl;
-    const int ir = rg * WD_RAD_NR + rl;
     h.dir_ok = d < n_dir;
-    h.active = h.dir_ok && ir < n_rad;
-    h.node = h.active ? (int64_t)ir * n_dir + d : 0;
-    const double r = h.active ? rad[ir] : 0.0;
-    h.rh = (float)r;
-    h.rlo = (float)(r - (double)h.rh);
-    h.rho = (float)(r * r);
-    h.r3 = (float)(r * r * r);
-    h.thr = h.active ? (float)((double)kDelta32 / r) : 3.402823466e38f;
-    h.rinv = h.active ? (float)(1.0 / r) : 0.0f;
-    h.dith = node_dither(h.node);
+#pragma unroll
+    for (int q = 0; q < WD_RAD_RPT; ++q) {
+        const int ir = rg * WD_RAD_NR + rl + q * WD_RAD_TPD;
+        h.active[q] = h.dir_ok && ir < n_rad;
+        h.node[q] = h.active[q] ? (int64_t)ir * n_dir + d : 0;
+        const double r = h.active[q] ? rad[ir] : 0.0;
+        h.rh[q] = (float)r;
+        h.rlo[q] = (float)(r - (double)h.rh[q]);
+        h.rho[q] = (float)(r * r);
+        h.r3[q] = (float)(r * r * r);
+        h.thr[q] = h.active[q] ? (float)((double)kDelta32 / r) : 3.402823466e38f;
+        h.rinv[q] = h.active[q] ? (float)(1.0 / r) : 0.0f;
+        h.dith[q] = node_dither(h.node[q]);
+    }
     return h;
 }
 
-// Sum of F_T over the triangle records [t0, t1) at this thread's node, in
+// F_T of record t at the thread's q-th radius (dithered phase, Taylor branch
+// as a polynomial in r^2 or the largest-gap branch)
+__device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
+                                            int q, float& fr, float& fi)
+{
+    // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
+    const float P = h.rh[q] * t.dmh;
+    const float e = fmaf(h.rh[q], t.dmh, -P);
+    const float lo = fmaf(h.rh[q], t.dml, fmaf(h.rlo[q], t.dmh, e));
+    const float tau = (P - rintf(P)) - h.dith[q];
+    if (t.gmax0 < h.thr[q]) {
+        const float rho = h.rho[q];
+        float sr = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
+        sr = fmaf(sr, rho, t.R[0]) * rho;
+        float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
+        si = fmaf(si, rho, t.I[0]) * h.r3[q];
+        taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi);
+    } else {
+        radial_divdiff(tl, tau, lo, h.rh[q], h.rinv[q], t, fr, fi);
+    }
+}
+
+// Sums of F_T over the triangle records [t0, t1) at the thread's nodes, in
 // tiles of WD_RAD_TILE triangles: the block first fills the tile's
 // (direction, triangle) records, then every thread runs over its direction's
 // row. Called by every thread of the block (barriers inside).
 __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const TabEntry* __restrict__ tl,
                                            const TriRecF* __restrict__ tris, int64_t t0, int64_t t1,
                                            const float* __restrict__ dir, int64_t n_dir, const RadThread& h,
-                                           double& acc_r, double& acc_i)
+                                           double* acc_r, double* acc_i)
 {
-    acc_r = 0.0;
-    acc_i = 0.0;
+#pragma unroll
+    for (int q = 0; q < WD_RAD_RPT; ++q) acc_r[q] = acc_i[q] = 0.0;
     for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
         const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
         const int cnt8 = (cnt + 7) & ~7;
@@ -741,41 +791,39 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
         const RadRec* rec = tile[h.dl];
         // plain float32 sums over groups of 8 pairs (dithered phases: random
         // roundings), Kahan across groups
-        Kahan kr, ki;
+        Kahan kr[WD_RAD_RPT], ki[WD_RAD_RPT];
         for (int j = 0; j < cnt8; j += 8) {
-            float br = 0.0f, bi = 0.0f;
+            float br[WD_RAD_RPT], bi[WD_RAD_RPT];
+#pragma unroll
+            for (int q = 0; q < WD_RAD_RPT; ++q) br[q] = bi[q] = 0.0f;
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 const RadRec& t = rec[j + jj];
-                // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
-                const float P = h.rh * t.dmh;
-                const float e = fmaf(h.rh, t.dmh, -P);
-                const float lo = fmaf(h.rh, t.dml, fmaf(h.rlo, t.dmh, e));
-                const float tau = (P - rintf(P)) - h.dith;
-                float fr, fi;
-                if (t.gmax0 < h.thr) {
-                    const float rho = h.rho;
-                    float sr = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
-                    sr = fmaf(sr, rho, t.R[0]) * rho;
-                    float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
-                    si = fmaf(si, rho, t.I[0]) * h.r3;
-                    taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi);
-                } else {
-                    radial_divdiff(tl, tau, lo, h.rh, h.rinv, t, fr, fi);
+#pragma unroll
+                for (int q = 0; q < WD_RAD_RPT; ++q) {
+                    float fr, fi;
+                    radial_pair(tl, t, h, q, fr, fi);
+                    br[q] += fr;
+                    bi[q] += fi;
                 }
-                br += fr;
-                bi += fi;
             }
-            kr.add(br);
-            ki.add(bi);
+#pragma unroll
+            for (int q = 0; q < WD_RAD_RPT; ++q) {
+                kr[q].add(br[q]);
+                ki[q].add(bi[q]);
+            }
         }
-        acc_r += kr.value();
-        acc_i += ki.value();
+#pragma unroll
+        for (int q = 0; q < WD_RAD_RPT; ++q) {
+            acc_r[q] += kr[q].value();
+            acc_i[q] += ki[q].value();
+        }
     }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a, const PairPlan p)
+__global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) pair_kernel_radial(const PairArgs a,
+                                                                                      const PairPlan p)
 {
     __shared__ __align__(16) RadRec tile[WD_RAD_ND][WD_RAD_TILE];
     __shared__ double red[WD_NPB / 32];
@@ -790,9 +838,10 @@ __global__ void __launch_bounds__(WD_NPB, 4) pair_kernel_radial(const PairArgs a
         const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
         int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
         if (t1 > a.T) t1 = a.T;
-        double acc_r, acc_i;
+        double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
         radial_sum(tile, tl, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
-        node_epilogue<true, MODE>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red, s_last);
+        node_epilogue<true, MODE, WD_RAD_RPT>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
+                                              s_last);
     }
 }
 
@@ -879,7 +928,7 @@ int resident_for(wd_ctx* ctx, int precision, int mode)
 // block is the same as in pair_kernel with one triangle chunk, so a request's
 // result does not depend on what else is in the batch.
 template <bool MIXED>
-__global__ void __launch_bounds__(WD_NPB, 4) serve_kernel(const ServeTable* __restrict__ head,
+__global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel(const ServeTable* __restrict__ head,
                                                        const ServeReq* __restrict__ reqs,
                                                        const ServeItem* __restrict__ items)
 {
@@ -900,18 +949,20 @@ __global__ void __launch_bounds__(WD_NPB, 4) serve_kernel(const ServeTable* __re
         const int64_t n = rq.n;
         if (MIXED && rq.rad) {  // block-uniform
             const RadThread h = radial_thread(rq.rad, rq.n_rad, rq.n_dir, item.nb, rq.n_rg);
-            double mr, mi;
+            double mr[WD_RAD_RPT], mi[WD_RAD_RPT];
             radial_sum(reinterpret_cast<RadRec(*)[WD_RAD_TILE]>(tbuf), exp_table_lane(etab),
                        static_cast<const TriRecF*>(rq.rec), 0, rq.T, rq.dir, rq.n_dir, h, mr, mi);
-            double sd, cd;
-            sincospi(2.0 * (double)h.dith, &sd, &cd);
-            const double r_ = mr * cd + mi * sd;
-            mi = mi * cd - mr * sd;
-            mr = r_;
             double term = 0.0;
-            if (h.active) {
-                const double dr = mr - rq.nu[2 * h.node], di = mi - rq.nu[2 * h.node + 1];
-                term = rq.W[h.node] * (dr * dr + di * di);
+#pragma unroll
+            for (int q = 0; q < WD_RAD_RPT; ++q) {
+                double sd, cd;
+                sincospi(2.0 * (double)h.dith[q], &sd, &cd);
+                const double r_ = mr[q] * cd + mi[q] * sd;
+                const double i_ = mi[q] * cd - mr[q] * sd;
+                if (h.active[q]) {
+                    const double dr = r_ - rq.nu[2 * h.node[q]], di = i_ - rq.nu[2 * h.node[q] + 1];
+                    term += rq.W[h.node[q]] * (dr * dr + di * di);
+                }
             }
             const double bsum = block_sum(term, red);
             if (threadIdx.x == 0) rq.blockD[item.nb] = bsum;
