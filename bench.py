@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--serve-queries", type=int, default=2000)
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint batch and fitting measurement")
     p.add_argument("--no-paper", action="store_true", help="skip the paper's cube-rule refinement ladder")
+    p.add_argument("--case", choices=["adjoint-n16"], default=None,
+                   help="run one fixed case for a profiler and exit: three mixed gradients of the n=16 "
+                        "adjoint-configuration mesh (seed 0) on the 192x64x96 rule")
     return p.parse_args()
 
 
@@ -380,8 +383,31 @@ def run_reference(args, cfg, queries, R):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(name):
+    """A fixed small case for ncu captures (no timing, no JSON line)."""
+    import torch
+
+    import paper_2304_06340_b300 as wd
+    ctx = wd.Context(0)
+    if name == "adjoint-n16":
+        R = synth.ADJOINT_RULE
+        rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+        v, t = synth.adjoint_mesh(16, 0)
+        dv, dt = torch.tensor(v, device="cuda"), torch.tensor(t, device="cuda", dtype=torch.int32)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.zeros_like(dv)
+        for _ in range(3):
+            wd.wd_distance_grad_dev(ctx.handle, rule, dv, dt, None, 1.0, wd.WD_MIXED, out, g)
+        torch.cuda.synchronize()
+        print("D %.12e |grad| %.12e" % (out.item(), g.norm().item()))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.case is not None:
+        profile_case(args.case)
+        return
     cfg, queries, R = workload(args.workload)
     if args.only_n is not None:
         queries = [q for q in queries if len(q[1]) == 20 * args.only_n ** 2]
