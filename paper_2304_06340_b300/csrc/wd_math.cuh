@@ -104,10 +104,15 @@ __device__ __forceinline__ const TabEntry* exp_table_lane(const TabEntry* tab)
     return tab + (threadIdx.x & (kTabRep - 1));
 }
 
+// kMagic = 1.5 * 2^23: tau * kTab + kMagic rounds to an integer in the low
+// bits. A caller may pass kMagic + s (s an integer, 0 <= s < kTab) instead:
+// the table index then moves by s while u stays the same, i.e. the result is
+// exp(-2 pi i (tau + s / kTab)) exactly (a phase shift by whole table steps).
+constexpr float kMagic = 12582912.0f;
+
 __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, float tau, float tlo,
-                                           float& er, float& ei)
+                                           float& er, float& ei, float magic = kMagic)
 {
-    const float magic = 12582912.0f;  // 1.5 * 2^23: rounds to an integer in the low bits
     const float km = fmaf(tau, (float)kTab, magic);
     const int idx = __float_as_int(km) & (kTab - 1);
     const float k = km - magic;                   // exact
@@ -128,6 +133,35 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, floa
     const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, xh, fmaf(t.ch, ds, t.sl)));
     er = c;   // exp(-i theta) = cos theta - i sin theta
     ei = -s;
+}
+
+// Per-(node, triangle tile) phase shift in whole table steps, s in [0, kTab):
+// a second dither that varies across the tiles of one node. At low frequency
+// the phases of all triangles of a node are close, so with the node's dither
+// alone their float32 roundings stay correlated; shifting each tile by its own
+// s (undone on the tile's sum in float64) makes the tiles' roundings
+// independent.
+__device__ __forceinline__ int tile_shift(int64_t node, int64_t tile)
+{
+    uint32_t h = (uint32_t)node * 0x9E3779B9u ^ ((uint32_t)tile * 0x85EBCA6Bu + 0x165667B1u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return (int)(h & (kTab - 1));
+}
+
+// Rotate a tile's float32 sum (sr, si), evaluated with tile shift s, back by
+// exp(+2 pi i s / kTab) in float64 (table entry s, replica 0, as a float pair)
+// and add it to (ar, ai).
+__device__ __forceinline__ void unshift_add(const TabEntry* __restrict__ tab, int s, double sr, double si,
+                                            double& ar, double& ai)
+{
+    const TabEntry e = tab[s * kTabRep];
+    const double c = (double)e.ch + (double)e.cl, sn = (double)e.sh + (double)e.sl;
+    ar += sr * c - si * sn;
+    ai += sr * sn + si * c;
 }
 
 // Kahan-compensated float32 accumulation: the per-tile sum of nearly equal

@@ -196,7 +196,8 @@ __device__ __forceinline__ void pair_f64(const NodeD& q, const TriRecD& t, doubl
 // pair with the largest gap, phases in turns about the dithered centroid
 // phase (tau, tlo); returns gamma G with gamma = gam + gam_lo.
 __device__ __forceinline__ void pair_mixed_divdiff(const TabEntry* __restrict__ tab, float tau, float tlo, float g1,
-                                                   float g2, float gam, float gam_lo, float& fr, float& fi)
+                                                   float g2, float gam, float gam_lo, float& fr, float& fi,
+                                                   float magic)
 {
     const float g3 = g2 - g1;
     const float a1 = fabsf(g1), a2 = fabsf(g2), a3 = fabsf(g3);
@@ -213,8 +214,8 @@ __device__ __forceinline__ void pair_mixed_divdiff(const TabEntry* __restrict__ 
     const float hQ = caseB ? 0.5f * g2 : 0.5f * g1;
     const float D = caseA ? g2 : (caseB ? g1 : g3);
     float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
-    expm_turns(tab, tau + offP, tlo, cP, sP);
-    expm_turns(tab, tau + offQ, tlo, cQ, sQ);
+    expm_turns(tab, tau + offP, tlo, cP, sP, magic);
+    expm_turns(tab, tau + offQ, tlo, cQ, sQ, magic);
     const float scP = sinc32(hP), scQ = sinc32(hQ);
     // S_P - S_Q, G = i (S_P - S_Q) / D
     const float dr = cP * scP - cQ * scQ;
@@ -234,10 +235,10 @@ __device__ __forceinline__ void pair_mixed_divdiff(const TabEntry* __restrict__ 
 // added inside the final rounding with gamma, where gamma c/2 is a full-width
 // product off the float grid.
 __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab, float tau, float tlo, float sr,
-                                               float si, float gam, float gam_lo, float& fr, float& fi)
+                                               float si, float gam, float gam_lo, float& fr, float& fi, float magic)
 {
     float c, s;
-    expm_turns(tab, tau, tlo, c, s);  // (c, s) = exp(-i (t_m - 2 pi dith))
+    expm_turns(tab, tau, tlo, c, s, magic);  // (c, s) = exp(-i (t_m - 2 pi dith + 2 pi shift))
     const float hc = 0.5f * c, hs = 0.5f * s;  // exact
     const float tr = fmaf(c, sr, -s * si);
     const float ti = fmaf(c, si, s * sr);
@@ -246,7 +247,7 @@ __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab,
 }
 
 __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, const NodeF& q, const TriRecF& t,
-                                           float& fr, float& fi)
+                                           float& fr, float& fi, float magic)
 {
     // centroid phase in turns: exact high products reduced mod 1, plus the low terms
     const float p0 = q.hx * t.mh[0], p1 = q.hy * t.mh[1], p2 = q.hz * t.mh[2];
@@ -306,10 +307,10 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
         im = fmaf(im, p, 1.0f / 120.0f);
         const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
         const float si = qq * fmaf(q2, iq, im);
-        taylor_combine(tab, tau, tlo, sr, si, t.gam, t.gam_lo, fr, fi);
+        taylor_combine(tab, tau, tlo, sr, si, t.gam, t.gam_lo, fr, fi, magic);
         return;
     }
-    pair_mixed_divdiff(tab, tau, tlo, g1, g2, t.gam, t.gam_lo, fr, fi);
+    pair_mixed_divdiff(tab, tau, tlo, g1, g2, t.gam, t.gam_lo, fr, fi, magic);
 }
 
 // ------------------------------------------------------------------ block reduction
@@ -522,22 +523,25 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
             __syncthreads();
             if (MIXED) {
                 // plain float32 sums over groups of 4 pairs (their phases are
-                // dithered, so the roundings are random), Kahan across groups
+                // dithered, so the roundings are random), Kahan across groups;
+                // each tile with its own phase shift
+                const int shift = tile_shift(node, tb / WD_TILE);
+                const float magic = kMagic + (float)shift;
                 Kahan kr, ki;
                 for (int j = 0; j < cnt4; j += 4) {
                     float br = 0.0f, bi = 0.0f;
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         float fr, fi;
-                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
+                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi,
+                                   magic);
                         br += fr;
                         bi += fi;
                     }
                     kr.add(br);
                     ki.add(bi);
                 }
-                acc_r += kr.value();
-                acc_i += ki.value();
+                unshift_add(etab, shift, kr.value(), ki.value(), acc_r, acc_i);
             } else {
                 for (int j = 0; j < cnt; ++j) {
                     double fr, fi;
@@ -657,11 +661,11 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const float* __res
 // (pair_mixed_divdiff) with its radius-independent choices taken from the
 // record; rinv = 1/r. Returns gamma G.
 __device__ __forceinline__ void radial_divdiff(const TabEntry* __restrict__ tl, float tau, float tlo, float r,
-                                               float rinv, const RadRec& t, float& fr, float& fi)
+                                               float rinv, const RadRec& t, float& fr, float& fi, float magic)
 {
     float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
-    expm_turns(tl, fmaf(r, t.oP, tau), tlo, cP, sP);
-    expm_turns(tl, fmaf(r, t.oQ, tau), tlo, cQ, sQ);
+    expm_turns(tl, fmaf(r, t.oP, tau), tlo, cP, sP, magic);
+    expm_turns(tl, fmaf(r, t.oQ, tau), tlo, cQ, sQ, magic);
     const float scP = sinc32(r * t.hP), scQ = sinc32(r * t.hQ);
     // 2 G = i (S_P - S_Q) (2 / D)
     const float dr = cP * scP - cQ * scQ;
@@ -681,10 +685,11 @@ __device__ __forceinline__ void radial_divdiff(const TabEntry* __restrict__ tl, 
 // taylor_combine. The product gamma_lo * tail (2^-24 of a zero-mean term
 // already below the float32 rounding of F) is left out.
 __device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__ tl, float tau, float tlo,
-                                                    float sr2, float si2, float g2, float l2, float& fr, float& fi)
+                                                    float sr2, float si2, float g2, float l2, float& fr, float& fi,
+                                                    float magic)
 {
     float c, s;
-    expm_turns(tl, tau, tlo, c, s);
+    expm_turns(tl, tau, tlo, c, s, magic);
     const float tr = fmaf(c, sr2, -s * si2);
     const float ti = fmaf(c, si2, s * sr2);
     fr = fmaf(g2, c, fmaf(g2, tr, l2 * c));
@@ -738,7 +743,7 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
 // F_T of record t at the thread's q-th radius (dithered phase, Taylor branch
 // as a polynomial in r^2 or the largest-gap branch)
 __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
-                                            int q, float& fr, float& fi)
+                                            int q, float& fr, float& fi, float magic)
 {
     // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
     const float P = h.rh[q] * t.dmh;
@@ -751,9 +756,9 @@ __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, con
         sr = fmaf(sr, rho, t.R[0]) * rho;
         float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
         si = fmaf(si, rho, t.I[0]) * h.r3[q];
-        taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi);
+        taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi, magic);
     } else {
-        radial_divdiff(tl, tau, lo, h.rh[q], h.rinv[q], t, fr, fi);
+        radial_divdiff(tl, tau, lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
     }
 }
 
@@ -761,11 +766,12 @@ __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, con
 // tiles of WD_RAD_TILE triangles: the block first fills the tile's
 // (direction, triangle) records, then every thread runs over its direction's
 // row. Called by every thread of the block (barriers inside).
-__device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const TabEntry* __restrict__ tl,
+__device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const TabEntry* __restrict__ tab,
                                            const TriRecF* __restrict__ tris, int64_t t0, int64_t t1,
                                            const float* __restrict__ dir, int64_t n_dir, const RadThread& h,
                                            double* acc_r, double* acc_i)
 {
+    const TabEntry* tl = exp_table_lane(tab);
 #pragma unroll
     for (int q = 0; q < WD_RAD_RPT; ++q) acc_r[q] = acc_i[q] = 0.0;
     for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
@@ -790,7 +796,10 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
         if (!h.dir_ok) continue;  // warp-uniform
         const RadRec* rec = tile[h.dl];
         // plain float32 sums over groups of 8 pairs (dithered phases: random
-        // roundings), Kahan across groups
+        // roundings), Kahan across groups. No per-tile phase shift here: on
+        // ball rules the weight spreads over many nodes and the shift's
+        // float64 rotation cost 3% of the throughput without a measurable
+        // gain in accuracy (see the per-node kernel for the lattice case)
         Kahan kr[WD_RAD_RPT], ki[WD_RAD_RPT];
         for (int j = 0; j < cnt8; j += 8) {
             float br[WD_RAD_RPT], bi[WD_RAD_RPT];
@@ -802,7 +811,7 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
 #pragma unroll
                 for (int q = 0; q < WD_RAD_RPT; ++q) {
                     float fr, fi;
-                    radial_pair(tl, t, h, q, fr, fi);
+                    radial_pair(tl, t, h, q, fr, fi, kMagic);
                     br[q] += fr;
                     bi[q] += fi;
                 }
@@ -839,7 +848,7 @@ __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) pair_kernel_r
         int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
         if (t1 > a.T) t1 = a.T;
         double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
-        radial_sum(tile, tl, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
+        radial_sum(tile, etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
         node_epilogue<true, MODE, WD_RAD_RPT>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
                                               s_last);
     }
@@ -950,8 +959,8 @@ __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel(
         if (MIXED && rq.rad) {  // block-uniform
             const RadThread h = radial_thread(rq.rad, rq.n_rad, rq.n_dir, item.nb, rq.n_rg);
             double mr[WD_RAD_RPT], mi[WD_RAD_RPT];
-            radial_sum(reinterpret_cast<RadRec(*)[WD_RAD_TILE]>(tbuf), exp_table_lane(etab),
-                       static_cast<const TriRecF*>(rq.rec), 0, rq.T, rq.dir, rq.n_dir, h, mr, mi);
+            radial_sum(reinterpret_cast<RadRec(*)[WD_RAD_TILE]>(tbuf), etab, static_cast<const TriRecF*>(rq.rec), 0,
+                       rq.T, rq.dir, rq.n_dir, h, mr, mi);
             double term = 0.0;
 #pragma unroll
             for (int q = 0; q < WD_RAD_RPT; ++q) {
@@ -1004,21 +1013,23 @@ __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel(
             }
             __syncthreads();
             if (MIXED) {
+                const int shift = tile_shift(node, tb / WD_TILE);
+                const float magic = kMagic + (float)shift;
                 Kahan kr, ki;
                 for (int j = 0; j < cnt4; j += 4) {
                     float br = 0.0f, bi = 0.0f;
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         float fr, fi;
-                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi);
+                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi,
+                                   magic);
                         br += fr;
                         bi += fi;
                     }
                     kr.add(br);
                     ki.add(bi);
                 }
-                acc_r += kr.value();
-                acc_i += ki.value();
+                unshift_add(etab, shift, kr.value(), ki.value(), acc_r, acc_i);
             } else {
                 for (int j = 0; j < cnt; ++j) {
                     double fr, fi;
