@@ -528,13 +528,16 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __
 constexpr int ADJ_RMAX = 256;  // radii per direction the radial adjoint stages
 constexpr int ADJ_TT = 32;     // triangles per tile of the radial adjoint (one warp of records)
 
+// 48 bytes: a quarter-warp's 128-bit loads of consecutive entries then fall
+// in 8 different bank groups (a 32-byte stride would pair them up)
 struct __align__(16) AdjRad {
     float rh, rlo;  // radius as a float pair
     float rho, r3;  // r^2, r^3
     float rinv;     // 1 / r
     float thr;      // Taylor branch while gmax0 < thr = DELTA / r
-    float pad[2];
+    float pad[6];
 };
+static_assert(sizeof(AdjRad) == 48, "AdjRad layout");
 
 // Residual rotated by the node's dither, direction-major: nd[d n_rad + ir] =
 // (Re, Im of r_k exp(2 pi i d_k), d_k, 0) for node k = ir n_dir + d.
@@ -679,7 +682,7 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
         a.r3 = (float)(r * r * r);
         a.rinv = (float)(1.0 / r);
         a.thr = (float)((double)kDeltaAM / r);
-        a.pad[0] = a.pad[1] = 0.0f;
+        for (int k = 0; k < 6; ++k) a.pad[k] = 0.0f;
         rt[i] = a;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -355,7 +355,9 @@ __device__ __noinline__ double origin_transform(const TriRecF* __restrict__ rec,
 // last chunk to finish does it), undo the mixed path's phase dither, then
 // write mu^ (FT) or subtract nu^, weight, write the residual (RESID) and reduce
 // D in fixed order (the last node block to finish adds the block sums).
-template <bool MIXED, int MODE, int K>
+// ORIGIN: the node list may contain xi = 0 (not for ball rules: their radii
+// are Gauss-Legendre nodes inside (0, R)).
+template <bool MIXED, int MODE, int K, bool ORIGIN = true>
 __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan& p, int64_t nb, int chunk,
                                               const int64_t* node, const bool* active, const float* dith,
                                               const double* acc_r, const double* acc_i, double* red, int& s_last)
@@ -404,12 +406,12 @@ __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan&
             const double r_ = mr[q] * cd + mi[q] * sd;
             mi[q] = mi[q] * cd - mr[q] * sd;
             mr[q] = r_;
-            origin[q] = active[q] && a.xi[node[q]] == 0.0 && a.xi[n + node[q]] == 0.0 &&
+            origin[q] = ORIGIN && active[q] && a.xi[node[q]] == 0.0 && a.xi[n + node[q]] == 0.0 &&
                         a.xi[2 * n + node[q]] == 0.0;
             any = any || origin[q];
         }
         // a node at the origin takes the exact total (block-uniform branch)
-        if (__syncthreads_or(any)) {
+        if (ORIGIN && __syncthreads_or(any)) {
             const double m0 = origin_transform(static_cast<const TriRecF*>(a.tris), a.T, red);
 #pragma unroll
             for (int q = 0; q < K; ++q)
@@ -849,8 +851,8 @@ __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) pair_kernel_r
         if (t1 > a.T) t1 = a.T;
         double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
         radial_sum(tile, etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
-        node_epilogue<true, MODE, WD_RAD_RPT>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
-                                              s_last);
+        node_epilogue<true, MODE, WD_RAD_RPT, false>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
+                                                     s_last);
     }
 }
 
