@@ -16,12 +16,17 @@
 // h_n differentiated in p and q) and the largest-gap divided difference (with
 // sinc' = (cos h - sinc h)/h, by its series for small h).
 //
-// Work items are (block of 128 triangles, chunk of frequency nodes); nodes are
-// staged in shared-memory tiles; each thread keeps the ten per-triangle sums
-// sum Re(conj r G), sum rho_i xi, sum rho_1 xi, sum rho_2 xi in float64. A
-// second kernel adds the chunks in fixed order and applies the geometry; a
-// third scatters the corner contributions to the vertices with float64 atomic
-// adds made exact by rounding to a per-(vertex, component) grid, so the
+// Three kernels produce the ten per-triangle sums sum Re(conj r G),
+// sum rho_i xi, sum rho_1 xi, sum rho_2 xi over a chunk of nodes:
+//   * adjoint_kernel_f64 (float64) and adjoint_kernel_mixed (mixed, explicit
+//     node lists): work items (block of 128 triangles, chunk of nodes), one
+//     thread per triangle over node tiles staged in shared memory;
+//   * adjoint_kernel_radial (mixed, ball rules): work items (tile of 32
+//     triangles, chunk of directions), a warp per (direction, triangle) with
+//     its lanes on the radii (see its comment).
+// A finalize kernel adds the chunks in fixed order and applies the geometry; a
+// scatter kernel adds the corner contributions to the vertices with float64
+// atomic adds made exact by rounding to a per-(vertex, component) grid, so the
 // gradient has the same bits on every run.
 #include <cstdint>
 

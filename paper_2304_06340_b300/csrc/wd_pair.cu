@@ -22,7 +22,13 @@
 //     over D >= DELTA.
 // Per node the transforms are summed over all triangles (linearity,
 // Sec. 3.1); the distance epilogue subtracts nu^, weights by
-// w_k (1 + |xi_k|^2)^(-s) and reduces (the quadrature of Eq. (sobolev_2)).
+// w_k (1 + c |xi_k|^2)^(-s) (c = 1, or 1/(4 pi^2) for the paper's lattice
+// rule) and reduces (the quadrature of Eq. (sobolev_2)).
+//
+// Kernels: pair_kernel (one node per thread; float64 path, and the mixed path
+// for explicit node lists and lattice rules), pair_kernel_radial (mixed path,
+// ball rules: per-(direction, triangle) records, radius per thread) and
+// serve_kernel (the serving loop's batched items, either form).
 #include <cstdint>
 #include <type_traits>
 
