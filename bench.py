@@ -391,6 +391,18 @@ def run_reference(args, cfg, queries, R):
     print(json.dumps(line), flush=True)
 
 
+def whole_job_rate(units_per_rank, seconds, world, dist=None, device="cpu"):
+    """Whole-job throughput over all ranks: every rank's units over the slowest
+    rank's time (max over ranks; a collective, so every rank calls it).
+    Returns (rate, seconds used)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = t.item()
+    return world * units_per_rank / seconds, seconds
+
+
 def profile_case(name):
     """A fixed small case for ncu captures (no timing, no JSON line)."""
     import torch
@@ -491,12 +503,8 @@ def main():
     clk = clocks.stop()
     wd.wd_sync(h, stream)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = tt.item()
-    value = world * pairs_per_step * args.steps / total_s / 1e9
+    rate, total_s = whole_job_rate(pairs_per_step * args.steps, sum(step_ms) / 1e3, world, dist, dev)
+    value = rate / 1e9
     # per-query kernel time (stage + pair kernel; the stage kernel is O(T) and under 0.1%)
     q_ms = [e0.elapsed_time(e1) for marks in qevs for (e0, e1, _) in marks]
     q_pairs = [T * n_eval for marks in qevs for (_, _, T) in marks]
@@ -533,8 +541,8 @@ def main():
     for _ in range(e2e_steps):
         for (v, t, s) in pinned:
             ctx.distance(rule, v, t, None, s, prec)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * pairs_per_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+    e2e_rate, _ = whole_job_rate(pairs_per_step * e2e_steps, time.perf_counter() - t0, world, dist, dev)
+    e2e = {"value": e2e_rate / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(sum(v.nbytes + t.nbytes for v, t, _ in pinned)),
            "d2h_bytes_per_step": 8 * len(pinned),
            "how": "wd_distance with pinned host mesh buffers, one synchronous call per query"}
