@@ -315,7 +315,8 @@ def wd_distance_dev_noalloc(xi_soa, w_geom, verts, tris, s, radius, center, prec
 # ------------------------------------------------------------------ serving
 def wd_serve_start(ctx, rules, precision=WD_MIXED, mem_cap_bytes=8 << 30, max_slots=64, max_pending=4096,
                    timeout_ms=0, pairs_per_launch=4_000_000_000):
-    """rules: list of (R, n_r, n_polar, n_azim, hermitian) tuples (at most 4)."""
+    """rules: list of (R, n_r, n_polar, n_azim, hermitian[, kind]) tuples (at most 4); kind defaults to
+    WD_RULE_BALL (WD_RULE_CUBE_TRAP: R = xi_max, n_r = M). Queries name their rule by R."""
     cfg = wd_serve_config()
     cfg.mem_cap_bytes = int(mem_cap_bytes)
     cfg.max_slots = int(max_slots)
@@ -324,8 +325,10 @@ def wd_serve_start(ctx, rules, precision=WD_MIXED, mem_cap_bytes=8 << 30, max_sl
     cfg.precision = int(precision)
     cfg.pairs_per_launch = int(pairs_per_launch)
     cfg.n_rules = len(rules)
-    for i, (R, n_r, n_p, n_a, herm) in enumerate(rules):
-        cfg.rules[i] = wd_rule_desc(WD_RULE_BALL, float(R), int(n_r), int(n_p), int(n_a), int(bool(herm)))
+    for i, r in enumerate(rules):
+        R, n_r, n_p, n_a, herm = r[:5]
+        kind = r[5] if len(r) > 5 else WD_RULE_BALL
+        cfg.rules[i] = wd_rule_desc(int(kind), float(R), int(n_r), int(n_p), int(n_a), int(bool(herm)))
     h = _vp()
     _check(_lib.wd_serve_start(ctx, ctypes.byref(cfg), ctypes.byref(h)))
     return h

@@ -127,3 +127,25 @@ def test_queued_queries_time_out(ctx):
         assert wd.wd_serve_stats(sv)["timeouts"] >= 1
     finally:
         wd.wd_serve_stop(sv)
+
+
+@pytest.mark.parametrize("prec", [wd.WD_MIXED, wd.WD_FP64])
+def test_lattice_rule_queries(ctx, prec):
+    # a cube (lattice) rule in the server: its per-node path (tile shifts, the
+    # origin node) gives what wd_distance gives on the same rule
+    rules = [(5.0, 16, 0, 0, True, wd.WD_RULE_CUBE_TRAP)]
+    cube = ctx.cube_rule(5.0, 16, True)
+    qs = [(synth.icosphere_recursive(k)[0], synth.icosphere_recursive(k)[1], 10.0) for k in (1, 2, 3)]
+    alone = [ctx.distance(cube, v, t, None, s, prec) for (v, t, s) in qs]
+    sv = wd.wd_serve_start(ctx.handle, rules, precision=prec, max_slots=4, pairs_per_launch=2_000_000)
+    try:
+        tickets = [wd.wd_serve_submit(sv, v, t, s, 5.0) for (v, t, s) in qs]
+        served = [wd.wd_serve_wait(sv, tk, 60000) for tk in tickets]
+    finally:
+        wd.wd_serve_stop(sv)
+    # float64: wd_distance splits these small rules' triangles into chunks, the
+    # server sums them in one pass; that order difference (1e-16 of mu^) reaches
+    # D amplified by |mu^| / |mu^ - nu^|, about 30 here
+    tol = 1e-10 if prec == wd.WD_FP64 else 1e-6
+    for a, b in zip(alone, served):
+        assert abs(a - b) <= tol * a, (a, b)
