@@ -48,6 +48,8 @@ def lib():
         L.or_divided_difference.argtypes = [_dp, ctypes.c_int, _dp, _dp]
         L.or_mesh_ft.argtypes = [_dp, _i64, _ip, _i64, _dp, _i64, _dp, _dp, ctypes.c_int]
         L.or_sphere_ft.argtypes = [_dp, _i64, ctypes.c_double, _dp, _dp, _dp]
+        L.or_simplex_atoms.argtypes = [_dp, _dp, _dp]
+        L.or_mesh_ft_atoms.argtypes = [_dp, _i64, _ip, _i64, _dp, _i64, _dp, _dp, ctypes.c_int]
         dist_args = [_dp, _dp, _i64, ctypes.c_double, ctypes.c_double, _dp, _i64, _ip, _i64, ctypes.c_int,
                      ctypes.c_double, _dp, _dp, _i64, _ip, _i64]
         L.or_distance.argtypes = dist_args + [_dp, _dp, ctypes.c_int]
@@ -137,6 +139,27 @@ def mesh_ft(verts, tris, xi, nthreads=None):
     rc = lib().or_mesh_ft(vp, len(v), tp, len(t), xp, n, _d(re)[1], _d(im)[1],
                           nthreads or default_threads())
     if rc != 0:
+        raise ValueError("triangle index out of range")
+    return re + 1j * im
+
+
+def simplex_atoms():
+    """The paper's 8 x 8 Gauss-Legendre atoms of the standard simplex: (u1, u2, q), 64 each."""
+    u1, u2, q = np.empty(64), np.empty(64), np.empty(64)
+    lib().or_simplex_atoms(_d(u1)[1], _d(u2)[1], _d(q)[1])
+    return u1, u2, q
+
+
+def mesh_ft_atoms(verts, tris, xi, nthreads=None):
+    """mu^ of the mesh's atomic approximation (64 atoms per triangle) at the nodes xi (N, 3)."""
+    v, vp = _d(verts)
+    t, tp = _i(tris)
+    x, xp = _d(xi)
+    n = len(x)
+    re = np.empty(n)
+    im = np.empty(n)
+    if lib().or_mesh_ft_atoms(vp, len(v), tp, len(t), xp, n, _d(re)[1], _d(im)[1],
+                              nthreads or default_threads()) != 0:
         raise ValueError("triangle index out of range")
     return re + 1j * im
 

@@ -364,6 +364,62 @@ int or_mesh_ft(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* The paper's atomic approximation of a triangle's surface measure (Sec. 3.1,
+ * Eqs. (change_variable), (change_variable_approx)): the 8-point Gauss-Legendre
+ * rule applied twice to the standard simplex Q_0 = {u1, u2 >= 0, u1 + u2 <= 1}
+ * as the iterated integral of u2 over [0, 1 - u1] inside u1 over [0, 1]:
+ * 64 atoms u = (x_i, (1 - x_i) x_j) with weights q = w_i w_j (1 - x_i), where
+ * (x, w) is the Gauss-Legendre rule moved to [0, 1]. On a triangle (a, b, c)
+ * they sit at a + u1 (b - a) + u2 (c - a) with weights q gamma.
+ * Writes the 64 atoms of Q_0 (u1, u2, q); returns 0.
+ * Pinned against the exact simplex moments: u1^a u2^b integrates to
+ * a! b! / (a + b + 2)!, exactly for a + b <= 14. */
+int or_simplex_atoms(double* u1, double* u2, double* q)
+{
+    double x[8], w[8];
+    if (or_gauss_legendre(8, x, w) != 0) return -1;
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            const ld xi = 0.5L * (1.0L + (ld)x[i]), wi = 0.5L * (ld)w[i];
+            const ld xj = 0.5L * (1.0L + (ld)x[j]), wj = 0.5L * (ld)w[j];
+            u1[8 * i + j] = (double)xi;
+            u2[8 * i + j] = (double)((1.0L - xi) * xj);
+            q[8 * i + j] = (double)(wi * wj * (1.0L - xi));
+        }
+    return 0;
+}
+
+/* mu^ of the atomic approximation above, sum over triangles and atoms of
+ * q gamma exp(-i xi.x), at n nodes (long double sums). */
+int or_mesh_ft_atoms(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                     const double* xi, int64_t n, double* re, double* im, int nthreads)
+{
+    if (!mesh_ok(nv, tris, nt)) return -1;
+    double u1[64], u2[64], q[64];
+    or_simplex_atoms(u1, u2, q);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (int64_t k = 0; k < n; ++k) {
+        const double* x = xi + 3 * k;
+        ld sr = 0.0L, si = 0.0L;
+        for (int64_t t = 0; t < nt; ++t) {
+            const double* a = verts + 3 * (int64_t)tris[3 * t];
+            const double* b = verts + 3 * (int64_t)tris[3 * t + 1];
+            const double* c = verts + 3 * (int64_t)tris[3 * t + 2];
+            const ld g = tri_gamma(a, b, c, NULL);
+            const ld ta = dotl(x, a), tb = dotl(x, b), tc = dotl(x, c);
+            for (int m = 0; m < 64; ++m) {
+                const ld ph = ta + (ld)u1[m] * (tb - ta) + (ld)u2[m] * (tc - ta);
+                sr += g * (ld)q[m] * cosl(ph);
+                si -= g * (ld)q[m] * sinl(ph);
+            }
+        }
+        re[k] = (double)sr;
+        im[k] = (double)si;
+    }
+    return 0;
+}
+
 /* Sphere of radius rho centred at c: nu^(xi) = 4 pi rho sin(rho |xi|)/|xi| exp(-i xi.c),
  * Eq. (ft_nsphere_sinc) in the angular convention, scaled and translated. */
 static void sphere_ft_ld(const double* xi, double rho, const double* c, ld* re, ld* im)

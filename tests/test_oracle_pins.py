@@ -349,6 +349,43 @@ def test_cube_rule_sphere_norm_as_the_paper_reports():
     assert dh == pytest.approx(df, rel=1e-14)
 
 
+def test_simplex_atoms_integrate_monomials_exactly():
+    # Sec. 3.1 (Eq. change_variable_approx with the 8-point Gauss-Legendre rule
+    # applied twice): exact for u1^a u2^b up to total degree 14, against the
+    # simplex moment a! b! / (a + b + 2)!
+    u1, u2, q = oracle.simplex_atoms()
+    assert np.all(q > 0) and np.all(u1 > 0) and np.all(u2 > 0) and np.all(u1 + u2 < 1)
+    for a in range(15):
+        for b in range(15 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert np.sum(q * u1 ** a * u2 ** b) == pytest.approx(exact, rel=1e-13), (a, b)
+    # total degree 16 is not integrated exactly by the iterated 8-point rule
+    for a, b in ((16, 0), (8, 8), (0, 16)):
+        exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+        assert abs(np.sum(q * u1 ** a * u2 ** b) - exact) > 1e-9 * exact, (a, b)
+
+
+def test_atomic_transform_approaches_the_exact_one():
+    # the atoms reproduce the exact triangle transform (Eq. simplex32_ft) with
+    # an error falling like (|xi| h)^16: tiny at |xi| h ~ 1, visible at ~10
+    v, t = synth.icosphere(2)
+    h = synth.mean_edge_length(v, t)
+    rng = np.random.default_rng(4)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    errs = []
+    for kh in (0.5, 2.0, 8.0, 16.0):
+        xi = dirs * (kh / h)
+        exact = oracle.mesh_ft(v, t, xi)
+        atoms = oracle.mesh_ft_atoms(v, t, xi)
+        errs.append(np.abs(atoms - exact).max() / (4 * np.pi))
+    assert errs[0] < 1e-15 and errs[1] < 1e-12
+    assert errs[2] < errs[3] and errs[3] > 1e-8
+    # at xi = 0 the atoms give the area
+    z = oracle.mesh_ft_atoms(v, t, np.zeros((1, 3)))
+    assert z[0].real == pytest.approx(oracle.mesh_ft(v, t, np.zeros((1, 3)))[0].real, rel=1e-15)
+
+
 def test_icosahedral_counts_and_total_area():
     for N in range(0, 5):
         v, t = synth.icosphere(2 ** N)
