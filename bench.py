@@ -368,7 +368,9 @@ def paper_bench(wd, ctx):
         r["D_fp64"] = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_FP64)
         r["mixed_vs_fp64"] = (r["D"] - r["D_fp64"]) / r["D_fp64"]
     t64 = time.perf_counter() - t64
-    return {"rule": "cube trapezoid xi_max=%g M=%d, hermitian (%d of %d nodes), paper's 2 pi convention"
+    atoms = atoms_bench(wd, ctx)
+    return {"atoms": atoms,
+            "rule": "cube trapezoid xi_max=%g M=%d, hermitian (%d of %d nodes), paper's 2 pi convention"
                     % (synth.PAPER_XI_MAX, synth.PAPER_M, n_eval, n_total),
             "s_paper": -synth.PAPER_S, "precision": "mixed",
             "sphere_norm2_rule_rel_err": abs(d_sphere - norm2) / norm2,
@@ -387,6 +389,35 @@ def paper_bench(wd, ctx):
                              "lowest-frequency nodes, so the mixed path's per-node rounding reaches D at "
                              "~1e-6 by N=5 and grows about 16x per level; rel_err = sqrt(D)/|sigma| moves by "
                              "half of that"}
+
+
+def atoms_bench(wd, ctx):
+    """The paper's 64-atom approximation of each triangle (Sec. 3.1) against the
+    exact transform, both float64, on the paper's lattice at M = 64 (Hermitian
+    half): per-node error relative to the area and the error it makes in D
+    (s = 10, the paper's H_{-10}), for T_1..T_3; and its pair rate."""
+    import math
+
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, 64, True)
+    xi, w = wd.wd_rule_copy_nodes(rule)
+    W = w * (1.0 + (xi ** 2).sum(1) / (4 * math.pi ** 2)) ** (-synth.PAPER_S)
+    r = np.linalg.norm(xi, axis=1)
+    nu = np.where(r > 0, 4 * math.pi * np.sin(r) / np.where(r > 0, r, 1.0), 4 * math.pi)
+    out, pairs, sec = [], 0, 0.0
+    for N in (1, 2, 3):
+        v, t = synth.icosphere_recursive(N)
+        exact = ctx.mesh_ft(rule, v, t, wd.WD_FP64)
+        t0 = time.perf_counter()
+        approx = ctx.mesh_ft_atoms(rule, v, t)
+        sec += time.perf_counter() - t0
+        pairs += len(t) * len(xi)
+        d_exact = float(np.sum(W * np.abs(exact - nu) ** 2))
+        d_atoms = float(np.sum(W * np.abs(approx - nu) ** 2))
+        out.append({"N": N, "triangles": len(t), "max_node_err_over_4pi": float(np.abs(approx - exact).max() / (4 * math.pi)),
+                    "D_rel_err": abs(d_atoms - d_exact) / d_exact})
+    return {"rule": "cube xi_max=%g M=64 hermitian (%d nodes), s=%g" % (synth.PAPER_XI_MAX, len(xi), synth.PAPER_S),
+            "levels": out, "gpairs_per_s_fp64": pairs / sec / 1e9,
+            "note": "host call incl. staging; 64 float64 exponentials per (triangle, node) pair"}
 
 
 def run_reference(args, cfg, queries, R):

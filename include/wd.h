@@ -158,6 +158,16 @@ wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule, const double* d_verts
                          const int32_t* d_tris, int64_t n_tris, int precision,
                          double* d_out_re, double* d_out_im, void* stream);
 
+/* The paper's atomic approximation of the same transform (Sec. 3.1, Eqs.
+ * (change_variable) and (change_variable_approx)). Each triangle is replaced by
+ * 64 weighted atoms from the 8-point Gauss-Legendre rule applied twice to the
+ * standard simplex as an iterated integral, and mu^ is their plane-wave sum,
+ * in float64. It approximates wd_mesh_ft with an error falling like
+ * (|xi| h)^16 for triangles of size h. It costs 64 exponentials per
+ * (triangle, node) pair where the exact formula needs one or two. Arguments,
+ * errors and outputs as for wd_mesh_ft. */
+wd_status wd_mesh_ft_atoms(wd_ctx* ctx, const wd_rule* rule, const wd_mesh* mesh, double* out_re, double* out_im);
+
 /* Transform of the surface measure of the sphere |x - center| = radius:
  * 4 pi radius sin(radius |xi|)/|xi| exp(-i xi.center) (Eq. (ft_nsphere_sinc),
  * angular convention, scaled and translated), in float64. */

@@ -81,6 +81,7 @@ _sig("wd_rule_copy_nodes", [_vp, _dp, _dp])
 _sig("wd_rule_free", [_vp], None)
 _sig("wd_mesh_ft", [_vp, _vp, ctypes.POINTER(wd_mesh), ctypes.c_int, _dp, _dp])
 _sig("wd_mesh_ft_dev", [_vp, _vp, _vp, _i64, _vp, _i64, ctypes.c_int, _vp, _vp, _vp])
+_sig("wd_mesh_ft_atoms", [_vp, _vp, ctypes.POINTER(wd_mesh), _dp, _dp])
 _sig("wd_sphere_ft", [_vp, _vp, ctypes.c_double, _dp, _dp, _dp])
 _sig("wd_sphere_ft_dev", [_vp, _vp, ctypes.c_double, _dp, _vp, _vp, _vp])
 _sig("wd_distance", [_vp, _vp, ctypes.POINTER(wd_mesh), ctypes.POINTER(wd_measure), ctypes.c_double,
@@ -236,6 +237,16 @@ def wd_mesh_ft(ctx, rule, verts, tris, precision=WD_FP64):
     im = np.empty(n)
     _check(_lib.wd_mesh_ft(ctx, rule, ctypes.byref(m), int(precision), re.ctypes.data_as(_dp),
                            im.ctypes.data_as(_dp)))
+    return re + 1j * im
+
+
+def wd_mesh_ft_atoms(ctx, rule, verts, tris):
+    """The paper's 64-atom approximation of the mesh transform (float64)."""
+    n, _ = wd_rule_info(rule)
+    m, keep = _host_mesh(verts, tris)
+    re = np.empty(n)
+    im = np.empty(n)
+    _check(_lib.wd_mesh_ft_atoms(ctx, rule, ctypes.byref(m), re.ctypes.data_as(_dp), im.ctypes.data_as(_dp)))
     return re + 1j * im
 
 
@@ -399,6 +410,9 @@ class Context:
 
     def mesh_ft(self, rule, verts, tris, precision=WD_FP64):
         return wd_mesh_ft(self.handle, rule, verts, tris, precision)
+
+    def mesh_ft_atoms(self, rule, verts, tris):
+        return wd_mesh_ft_atoms(self.handle, rule, verts, tris)
 
     def sphere_ft(self, rule, radius=1.0, center=(0.0, 0.0, 0.0)):
         return wd_sphere_ft(self.handle, rule, radius, center)

@@ -269,6 +269,40 @@ extern "C" wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule_c, const do
     return run_core(ctx, rule, L, precision, MODE_FT, d_verts, nv, d_tris, nt, nullptr, 0.0, d_re, d_im, s);
 }
 
+extern "C" wd_status wd_mesh_ft_atoms(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mesh, double* out_re,
+                                      double* out_im)
+{
+    WdRange nvtx_range("wd_mesh_ft_atoms");
+    wd_status st = check_common(ctx, rule_c, WD_FP64);
+    if (st != WD_OK) return st;
+    std::string why;
+    WD_CHECK(host_mesh_ok(mesh, &why), WD_EINVAL, why);
+    const int64_t n = rule_c->n_eval;
+    WD_CHECK(n == 0 || (out_re && out_im), WD_EINVAL, "null output array");
+    if ((st = wd_activate(ctx)) != WD_OK) return st;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    const int64_t nt = mesh->n_tris;
+    size_t ov = 0, ot = align_up(sizeof(double) * 3 * mesh->n_verts);
+    size_t orc = ot + align_up(sizeof(int32_t) * 3 * nt);
+    size_t oo = orc + align_up(sizeof(TriRecD) * (size_t)(nt > 0 ? nt : 1));
+    size_t end = oo + 2 * align_up(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if ((st = wd_ws_reserve(ctx, end)) != WD_OK) return st;
+    cudaStream_t s = 0;
+    if ((st = upload_mesh(ctx, mesh, ov, ot, s)) != WD_OK) return st;
+    void* rec = ctx->ws + orc;
+    if ((st = wd_launch_stage(ctx, WD_FP64, reinterpret_cast<const double*>(ctx->ws + ov), mesh->n_verts,
+                              reinterpret_cast<const int32_t*>(ctx->ws + ot), nt, 1.0, rec, 0, s)) != WD_OK)
+        return st;
+    double* d_re = reinterpret_cast<double*>(ctx->ws + oo);
+    double* d_im = reinterpret_cast<double*>(ctx->ws + oo + align_up(sizeof(double) * (size_t)(n > 0 ? n : 1)));
+    if ((st = wd_launch_atoms(ctx, rule_c->d_xi, n, rec, nt, d_re, d_im, s)) != WD_OK) return st;
+    if (n > 0) {
+        WD_CUDA(cudaMemcpyAsync(out_re, d_re, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        WD_CUDA(cudaMemcpyAsync(out_im, d_im, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
+    return finish_host(ctx, s);
+}
+
 extern "C" wd_status wd_mesh_ft(wd_ctx* ctx, const wd_rule* rule_c, const wd_mesh* mesh, int precision,
                                 double* out_re, double* out_im)
 {

@@ -250,5 +250,11 @@ wd_status wd_launch_serve(wd_ctx* ctx, int precision, int grid, const ServeTable
                           double* d_results, cudaStream_t st);
 int wd_serve_resident(wd_ctx* ctx, int precision);
 
+// Gauss-Legendre nodes and weights on [-1, 1], ascending (host, long double)
+void wd_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w);
+// the paper's atomic transform (wd_atoms.cu): d_rec holds float64 records
+wd_status wd_launch_atoms(wd_ctx* ctx, const double* d_xi, int64_t n, const void* d_rec, int64_t T, double* d_re,
+                          double* d_im, cudaStream_t st);
+
 wd_status wd_launch_weights(wd_ctx* ctx, const double* d_xi, const double* d_wg, int64_t n,
                             double s, double wscale, double* d_w, cudaStream_t st);

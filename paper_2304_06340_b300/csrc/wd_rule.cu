@@ -437,3 +437,5 @@ void wd_release_all_rules(wd_ctx* ctx)
     ctx->rules.clear();
     ctx->explicit_rules.clear();
 }
+
+void wd_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) { legendre_rule(n, x, w); }
