@@ -163,7 +163,7 @@ wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule, const double* d_verts
  * 64 weighted atoms from the 8-point Gauss-Legendre rule applied twice to the
  * standard simplex as an iterated integral, and mu^ is their plane-wave sum,
  * in float64. It approximates wd_mesh_ft with an error falling like
- * (|xi| h)^16 for triangles of size h. It costs 64 exponentials per
+ * (|xi| h)^15 for triangles of size h. It costs 64 exponentials per
  * (triangle, node) pair where the exact formula needs one or two. Arguments,
  * errors and outputs as for wd_mesh_ft. */
 wd_status wd_mesh_ft_atoms(wd_ctx* ctx, const wd_rule* rule, const wd_mesh* mesh, double* out_re, double* out_im);

@@ -6,7 +6,7 @@
 // [0, 1]: u = (x_i, (1 - x_i) x_j), q = w_i w_j (1 - x_i), (x, w) the rule on
 // [0, 1]. The transform is the atoms' plane-wave sum, in float64. It
 // approximates the exact transform of wd_pair.cu with an error that falls like
-// (|xi| h)^16 on triangles of size h, at 64 exponentials per (triangle, node)
+// (|xi| h)^15 on triangles of size h, at 64 exponentials per (triangle, node)
 // pair where the exact formula needs one or two.
 #include <cmath>
 #include <mutex>

@@ -359,15 +359,16 @@ def test_simplex_atoms_integrate_monomials_exactly():
         for b in range(15 - a):
             exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
             assert np.sum(q * u1 ** a * u2 ** b) == pytest.approx(exact, rel=1e-13), (a, b)
-    # total degree 16 is not integrated exactly by the iterated 8-point rule
-    for a, b in ((16, 0), (8, 8), (0, 16)):
+    # total degree 15 is not: the outer integrand u1^a (1 - u1)^(b+1) / (b+1)
+    # then has degree 16 > 2 * 8 - 1
+    for a, b in ((15, 0), (8, 7), (0, 15)):
         exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
         assert abs(np.sum(q * u1 ** a * u2 ** b) - exact) > 1e-9 * exact, (a, b)
 
 
 def test_atomic_transform_approaches_the_exact_one():
     # the atoms reproduce the exact triangle transform (Eq. simplex32_ft) with
-    # an error falling like (|xi| h)^16: tiny at |xi| h ~ 1, visible at ~10
+    # an error falling like (|xi| h)^15: tiny at |xi| h ~ 1, visible at ~10
     v, t = synth.icosphere(2)
     h = synth.mean_edge_length(v, t)
     rng = np.random.default_rng(4)
