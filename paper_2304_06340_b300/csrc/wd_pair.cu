@@ -245,11 +245,14 @@ __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab,
 {
     float c, s;
     expm_turns(tab, tau, tlo, c, s, magic);  // (c, s) = exp(-i (t_m - 2 pi dith + 2 pi shift))
-    const float hc = 0.5f * c, hs = 0.5f * s;  // exact
-    const float tr = fmaf(c, sr, -s * si);
-    const float ti = fmaf(c, si, s * sr);
-    fr = fmaf(gam, hc, fmaf(gam, tr, gam_lo * (hc + tr)));
-    fi = fmaf(gam, hs, fmaf(gam, ti, gam_lo * (hs + ti)));
+    // gamma (c + i s)(1/2 + sr + i si) = g2 (c + i s) + (c + i s)(ar + i ai) with
+    // g2 = gamma/2, ar = gamma sr + gamma_lo/2, ai = gamma si; gamma_lo times
+    // the tail (2^-24 of a zero-mean term) is left out
+    const float g2 = 0.5f * gam;                    // exact
+    const float ar = fmaf(gam, sr, 0.5f * gam_lo);
+    const float ai = gam * si;
+    fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
+    fi = fmaf(g2, s, fmaf(s, ar, c * ai));
 }
 
 __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, const NodeF& q, const TriRecF& t,
@@ -584,8 +587,8 @@ struct __align__(16) RadRec {
     float gmax0;         // largest |gap| per unit radius
     float g2;            // gamma / 2, high part (0 for padding)
     float l2;            // gamma / 2, low part
-    float R[6];          // real tail coefficients R1..R6, times 2
-    float I[5];          // imaginary tail coefficients I0..I4, times 2
+    float R[6];          // real tail coefficients R1..R6, times gamma
+    float I[5];          // imaginary tail coefficients I0..I4, times gamma
     // divided-difference branch, per unit radius: phase offsets of the two
     // first differences about the centroid (turns), their half gaps, and
     // 2 / (largest gap); the case (which vertex pair has the largest gap)
@@ -648,8 +651,11 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const float* __res
     o.I[2] = 3.0f * q0 * p2 * (1.0f / 362880.0f);
     o.I[3] = -q0 * fmaf(4.0f, p3, q02) * (1.0f / 39916800.0f);
     o.I[4] = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
-    for (int k = 0; k < 6; ++k) o.R[k] *= 2.0f;  // exact
-    for (int k = 0; k < 5; ++k) o.I[k] *= 2.0f;
+    // scaled by gamma (high part), so that the pair's tail comes out already
+    // multiplied by gamma; the smallest scaled coefficients reach the float32
+    // subnormal range only where their terms are far below the rounding of F
+    for (int k = 0; k < 6; ++k) o.R[k] *= t.gam;
+    for (int k = 0; k < 5; ++k) o.I[k] *= t.gam;
     // largest gap: A = (a, c) with d2, B = (a, b) with d1, C = (b, c) with d3,
     // as in pair_mixed_divdiff
     const bool caseA = (a2 >= a1) && (a2 >= a3);
@@ -685,23 +691,22 @@ __device__ __forceinline__ void radial_divdiff(const TabEntry* __restrict__ tl, 
     fi = fmaf(t.g2, gi, t.l2 * gi);
 }
 
-// Taylor branch end for the radial kernel, with the doubled tail 2 (sr + i si)
-// and g2 = gamma/2, l2 = gamma_lo/2:
+// Taylor branch end for the radial kernel. With g2 = gamma/2 and
+// l2 = gamma_lo/2 (both exact), the gamma-scaled tail gamma (sr + i si) as
+// (ar - l2) + i ai, i.e. ar = l2 + gamma sr:
 //     F = gamma (c + i s)(1/2 + sr + i si)
-//       = (gamma/2)(c + i s) + (gamma/2)(c + i s)(2 sr + 2 i si) + (gamma_lo/2)(c + i s),
-// gamma/2 and gamma_lo/2 exact, all in one final rounding per component as in
-// taylor_combine. The product gamma_lo * tail (2^-24 of a zero-mean term
-// already below the float32 rounding of F) is left out.
+//       = g2 (c + i s) + (c + i s)(ar + i ai),
+// in one final rounding per component as in taylor_combine. The product
+// gamma_lo * tail (2^-24 of a zero-mean term already below the float32
+// rounding of F) is left out.
 __device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__ tl, float tau, float tlo,
-                                                    float sr2, float si2, float g2, float l2, float& fr, float& fi,
+                                                    float ar, float ai, float g2, float& fr, float& fi,
                                                     float magic)
 {
     float c, s;
     expm_turns(tl, tau, tlo, c, s, magic);
-    const float tr = fmaf(c, sr2, -s * si2);
-    const float ti = fmaf(c, si2, s * sr2);
-    fr = fmaf(g2, c, fmaf(g2, tr, l2 * c));
-    fi = fmaf(g2, s, fmaf(g2, ti, l2 * s));
+    fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
+    fi = fmaf(g2, s, fmaf(s, ar, c * ai));
 }
 
 // One thread's nodes in a radial node block: block nb covers directions
@@ -760,11 +765,11 @@ __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, con
     const float tau = (P - rintf(P)) - h.dith[q];
     if (t.gmax0 < h.thr[q]) {
         const float rho = h.rho[q];
-        float sr = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
-        sr = fmaf(sr, rho, t.R[0]) * rho;
-        float si = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
-        si = fmaf(si, rho, t.I[0]) * h.r3[q];
-        taylor_combine_half(tl, tau, lo, sr, si, t.g2, t.l2, fr, fi, magic);
+        float ar = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
+        ar = fmaf(fmaf(ar, rho, t.R[0]), rho, t.l2);
+        float ai = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
+        ai = fmaf(ai, rho, t.I[0]) * h.r3[q];
+        taylor_combine_half(tl, tau, lo, ar, ai, t.g2, fr, fi, magic);
     } else {
         radial_divdiff(tl, tau, lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
     }
