@@ -749,6 +749,19 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
         h.thr[q] = h.active[q] ? (float)((double)kDelta32 / r) : 3.402823466e38f;
         h.rinv[q] = h.active[q] ? (float)(1.0 / r) : 0.0f;
         h.dith[q] = node_dither(h.node[q]);
+        // A warp holds 32 consecutive radii of one direction, and the branch
+        // test r gmax0 < DELTA splits it wherever a record's seam falls inside
+        // its radius range; the split warp then runs both branches. Where the
+        // warp's radii lie within a factor of 2 (every warp but the innermost
+        // ones), the whole warp takes the branch of its largest radius
+        // instead: Taylor only where every lane's gap is below DELTA (so the
+        // remainder bound holds), the divided difference otherwise, which
+        // then sees gaps of at least DELTA r_min / r_max > DELTA / 2.
+        const unsigned int umax = __reduce_max_sync(0xffffffffu, h.active[q] ? __float_as_uint(h.rh[q]) : 0u);
+        const unsigned int umin =
+            __reduce_min_sync(0xffffffffu, h.active[q] ? __float_as_uint(h.rh[q]) : 0x7f7fffffu);
+        const float rmax = __uint_as_float(umax), rmin = __uint_as_float(umin);
+        if (rmax > 0.0f && rmax < 2.0f * rmin) h.thr[q] = (float)((double)kDelta32 / (double)rmax);
     }
     return h;
 }
