@@ -686,7 +686,19 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
         a.rho = (float)(r * r);
         a.r3 = (float)(r * r * r);
         a.rinv = (float)(1.0 / r);
-        a.thr = (float)((double)kDeltaAM / r);
+        // Lanes take radii i = lane + 32 k, so the radii of one pass of a warp
+        // are the group of 32 consecutive ones holding i. Where the group's
+        // radii lie within a factor of 2, all of them take the branch of the
+        // group's largest radius (as in the radial pair kernel), so that no
+        // warp runs both: Taylor only below DELTA, the largest-gap branch
+        // from DELTA / 2 up.
+        const int g0 = i & ~31, g1 = min(g0 + 32, n_rad);
+        double rmin = rad[g0], rmax = rad[g0];
+        for (int k = g0 + 1; k < g1; ++k) {
+            rmin = fmin(rmin, rad[k]);
+            rmax = fmax(rmax, rad[k]);
+        }
+        a.thr = (float)((double)kDeltaAM / (rmax < 2.0 * rmin ? rmax : r));
         for (int k = 0; k < 6; ++k) a.pad[k] = 0.0f;
         rt[i] = a;
     }
