@@ -10,6 +10,7 @@
 // pair where the exact formula needs one or two.
 #include <cmath>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "wd_internal.h"
@@ -23,7 +24,7 @@ constexpr int ATOM_TILE = 128;
 __constant__ double c_u1[kAtoms], c_u2[kAtoms], c_q[kAtoms];
 
 std::mutex g_atoms_mu;
-bool g_atoms_ready[64] = {false};
+std::set<int> g_atoms_ready;  // devices whose constant memory holds the atoms
 
 // One node per thread; triangle records (float64 staging) in shared-memory
 // tiles; per (node, triangle) the vertex phase t_a = xi.a and the two edge
@@ -79,8 +80,7 @@ __global__ void __launch_bounds__(ATOM_TPB) atoms_kernel(const double* __restric
 wd_status atoms_setup(wd_ctx* ctx)
 {
     std::lock_guard<std::mutex> lk(g_atoms_mu);
-    const int dev = ctx->device & 63;
-    if (g_atoms_ready[dev]) return WD_OK;
+    if (g_atoms_ready.count(ctx->device)) return WD_OK;
     std::vector<double> x, w;
     wd_legendre_rule(8, x, w);
     double u1[kAtoms], u2[kAtoms], q[kAtoms];
@@ -95,7 +95,7 @@ wd_status atoms_setup(wd_ctx* ctx)
     WD_CUDA(cudaMemcpyToSymbol(c_u1, u1, sizeof(u1)));
     WD_CUDA(cudaMemcpyToSymbol(c_u2, u2, sizeof(u2)));
     WD_CUDA(cudaMemcpyToSymbol(c_q, q, sizeof(q)));
-    g_atoms_ready[dev] = true;
+    g_atoms_ready.insert(ctx->device);
     return WD_OK;
 }
 
