@@ -46,6 +46,8 @@ wd_status check_nu(const wd_measure* nu)
     WD_CHECK(nu->kind == WD_NU_MESH, WD_EINVAL, "unknown reference-measure kind");
     WD_CHECK(nu->mesh, WD_EINVAL, "WD_NU_MESH needs a mesh");
     WD_CHECK(nu->mesh->n_verts >= 0 && nu->mesh->n_tris >= 0, WD_EINVAL, "negative mesh size");
+    WD_CHECK(nu->mesh->n_tris == 0 || (nu->mesh->verts && nu->mesh->tris), WD_EINVAL,
+             "reference mesh: null mesh array");
     return WD_OK;
 }
 
@@ -442,6 +444,38 @@ extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_me
     return finish_host(ctx, strm);
 }
 
+// Scratch layout of the gradient from offset `base`: the forward pass's
+// records, chunk partials and block sums, then the residual, the float64
+// records of the adjoint, its per-(chunk, triangle) sums, the scatter scratch
+// and the radial adjoint's tables.
+struct GradLayout {
+    CoreLayout core;
+    AdjPlan ap;
+    size_t res = 0, rec64 = 0, adj = 0, sc = 0, rad = 0, end = 0;
+};
+
+static GradLayout grad_layout(wd_ctx* ctx, const wd_rule* rule, int precision, int64_t nt, int64_t nt2, int64_t nv,
+                              size_t base)
+{
+    GradLayout G;
+    const int64_t n = rule->n_eval;
+    G.core = core_layout(ctx, rule, precision, MODE_RESID, nt + nt2, base);
+    wd_plan_adjoint_rule(ctx, rule, precision, nt, &G.ap);
+    size_t off = G.core.end;
+    G.res = off;
+    off += align_up(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    G.rec64 = off;
+    off += align_up(sizeof(TriRecD) * (size_t)(nt > 0 ? nt : 1));
+    G.adj = off;
+    off += align_up(sizeof(double) * 10 * (size_t)(G.ap.nchunks > 0 ? G.ap.nchunks : 1) * (size_t)(nt > 0 ? nt : 1));
+    G.sc = off;
+    off += align_up(wd_adjoint_scatter_bytes(nt, nv));
+    G.rad = off;
+    if (G.ap.radial) off += align_up(wd_adjoint_radial_bytes(rule));
+    G.end = off;
+    return G;
+}
+
 // Gradient core on device pointers: forward pass in `precision` writing D and
 // the residual 2 W (mu^ - nu^), then the adjoint in the same precision over
 // mu's triangles.
@@ -451,24 +485,13 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
 {
     const int64_t nt2 = nu->kind == WD_NU_MESH ? nu->mesh->n_tris : 0;
     const int64_t n = rule->n_eval;
-    CoreLayout L = core_layout(ctx, rule, precision, MODE_RESID, nt + nt2, base);
-    AdjPlan ap;
-    wd_plan_adjoint_rule(ctx, rule, precision, nt, &ap);
-    size_t off = L.end;
-    const size_t o_res = off;
-    off += align_up(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
-    const size_t o_rec64 = off;
-    off += align_up(sizeof(TriRecD) * (size_t)(nt > 0 ? nt : 1));
-    const size_t o_adj = off;
-    off += align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) * (size_t)(nt > 0 ? nt : 1));
-    const size_t o_sc = off;
-    off += align_up(wd_adjoint_scatter_bytes(nt, nv));
-    const size_t o_rad = off;
-    if (ap.radial) off += align_up(wd_adjoint_radial_bytes(rule));
-    wd_status st_ = wd_ws_reserve(ctx, off);
+    const GradLayout G = grad_layout(ctx, rule, precision, nt, nt2, nv, base);
+    const CoreLayout& L = G.core;
+    const AdjPlan& ap = G.ap;
+    wd_status st_ = wd_ws_reserve(ctx, G.end);
     if (st_ != WD_OK) return st_;
     if ((st_ = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st_;
-    double* resid = reinterpret_cast<double*>(ctx->ws + o_res);
+    double* resid = reinterpret_cast<double*>(ctx->ws + G.res);
     if (n > 0) WD_CUDA(cudaMemsetAsync(resid, 0, sizeof(double) * 2 * n, st));
     if (nv > 0) WD_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(double) * 3 * nv, st));
     // forward (same staging as the distance), with the residual written per node
@@ -498,11 +521,11 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     }
     if ((st_ = wd_launch_pair(ctx, precision, MODE_RESID, L.plan, a, st)) != WD_OK) return st_;
     // adjoint over mu's triangles, staged in float64
-    void* rec64 = ctx->ws + o_rec64;
+    void* rec64 = ctx->ws + G.rec64;
     if ((st_ = wd_launch_stage(ctx, WD_FP64, d_verts, nv, d_tris, nt, 1.0, rec64, 0, st)) != WD_OK) return st_;
     return wd_launch_adjoint(ctx, precision, ap, rule, resid, rec64, precision == WD_MIXED ? rec : nullptr, nt,
-                             ap.radial ? ctx->ws + o_rad : nullptr, reinterpret_cast<double*>(ctx->ws + o_adj),
-                             ctx->ws + o_sc, d_tris, nv, d_grad, st);
+                             ap.radial ? ctx->ws + G.rad : nullptr, reinterpret_cast<double*>(ctx->ws + G.adj),
+                             ctx->ws + G.sc, d_tris, nv, d_grad, st);
 }
 
 extern "C" wd_status wd_distance_grad_dev(wd_ctx* ctx, const wd_rule* rule_c, const double* d_verts,
@@ -551,20 +574,10 @@ extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const 
     // before it touches any of it, and the uploads are issued after that
     if ((st = wd_ws_reserve(ctx, base)) != WD_OK) return st;
     cudaStream_t strm = 0;
-    // grad_core may reallocate the scratch, so size it first with a dry layout
-    {
-        const int64_t nt2 = m2 ? m2->n_tris : 0;
-        CoreLayout L = core_layout(ctx, rule, precision, MODE_RESID, mu->n_tris + nt2, base);
-        AdjPlan ap;
-        wd_plan_adjoint_rule(ctx, rule, precision, mu->n_tris, &ap);
-        size_t need = L.end + align_up(sizeof(double) * 2 * (size_t)(rule->n_eval > 0 ? rule->n_eval : 1)) +
-                      align_up(sizeof(TriRecD) * (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
-                      align_up(sizeof(double) * 10 * (size_t)(ap.nchunks > 0 ? ap.nchunks : 1) *
-                               (size_t)(mu->n_tris > 0 ? mu->n_tris : 1)) +
-                      align_up(wd_adjoint_scatter_bytes(mu->n_tris, mu->n_verts)) +
-                      (ap.radial ? align_up(wd_adjoint_radial_bytes(rule)) : 0);
-        if ((st = wd_ws_reserve(ctx, need)) != WD_OK) return st;
-    }
+    // grad_core reserves the scratch for its own layout, and a reallocation
+    // there would lose the uploads; reserve that same layout before uploading
+    const GradLayout G = grad_layout(ctx, rule, precision, mu->n_tris, m2 ? m2->n_tris : 0, mu->n_verts, base);
+    if ((st = wd_ws_reserve(ctx, G.end)) != WD_OK) return st;
     if ((st = upload_mesh(ctx, mu, ov, ot, strm)) != WD_OK) return st;
     wd_mesh dm2{};
     wd_measure dnu = *nu;
