@@ -461,6 +461,42 @@ def test_gradient_matches_central_differences():
     assert np.abs(g0).max() == 0.0
 
 
+def _central_differences(f, v, h=1e-6):
+    fd = np.zeros_like(v)
+    for i in range(len(v)):
+        for j in range(3):
+            vp = v.copy()
+            vm = v.copy()
+            vp[i, j] += h
+            vm[i, j] -= h
+            fd[i, j] = (f(vp) - f(vm)) / (2 * h)
+    return fd
+
+
+@pytest.mark.parametrize("case", ["other_mesh", "shifted_sphere", "paper_lattice"])
+def test_gradient_matches_central_differences_for_other_references(case):
+    # The residual is zero when nu is mu itself, so that pin cannot see the
+    # reference measure's part of the gradient; here nu differs from mu: a
+    # second mesh, a sphere of another radius and centre, and the paper's
+    # lattice with its 1/(4 pi^2) weight scale (Eqs. for the cube rule, Sec. 3.2)
+    v, t = synth.icosphere(1)
+    v = synth.jitter_isotropic(v, 0.02, 11)
+    xi, w = oracle.ball_rule(8.0, 10, 6, 8, True)
+    s, nu, wscale = 1.0, None, 1.0
+    if case == "other_mesh":
+        v2, t2 = synth.icosphere(2)
+        nu = ("mesh", synth.jitter_isotropic(v2, 0.01, 12), t2)
+    elif case == "shifted_sphere":
+        nu = ("sphere", 0.9, (0.1, -0.05, 0.02))
+    else:
+        xi, w = oracle.cube_rule(1.5, 8, True)
+        s, wscale = 2.0, oracle.PAPER_WSCALE
+    d, g = oracle.distance_grad(xi, w, s, v, t, nu=nu, wscale=wscale)
+    assert d == pytest.approx(oracle.distance(xi, w, s, v, t, nu=nu, wscale=wscale), rel=1e-15)
+    fd = _central_differences(lambda x: oracle.distance(xi, w, s, x, t, nu=nu, wscale=wscale), v)
+    assert np.linalg.norm(fd - g) < 1e-7 * np.linalg.norm(g)
+
+
 def test_invalid_mesh_is_rejected():
     v, t = synth.icosphere(1)
     bad = t.copy()
