@@ -98,10 +98,13 @@ __global__ void stage_kernel(const double* __restrict__ verts, int64_t nv,
 // ------------------------------------------------------------------ shared pieces
 // Taylor branch bounds: below a largest gap DELTA the centred phases satisfy
 // |y| <= 2 DELTA / 3. float64: DELTA = 1, series to n = 18 (remainder < 1e-18);
-// mixed: DELTA = 3, series to n = 12 (p <= 3, remainder < 3e-9).
+// mixed: DELTA = 3, series to n = 12 (p <= 3, remainder < 3e-9); in the
+// radial kernel also DELTA_S = 1.5 with the series to n = 9 (remainder
+// < 1e-9, the worst over sampled triangle shapes).
 constexpr double kDelta64 = 1.0;
 constexpr int kTerms64 = 18;
 constexpr float kDelta32 = 3.0f;
+constexpr float kDeltaShort32 = 1.5f;
 
 // 1/(n+2)! for n = 0..22
 __device__ constexpr double kInvFact2[23] = {
@@ -582,13 +585,17 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const Pa
 // float64 pipe of this GPU is too narrow for it), then every thread runs
 // over the tile with its own radius. A warp holds 32 radii of one direction,
 // so the record loads are broadcasts.
+// The fields are grouped by 16 bytes in the order the branches read them:
+// the short Taylor form reads the first three groups, the full one the first
+// four, the divided difference the first and the last three.
 struct __align__(16) RadRec {
     float dmh, dml;      // omega.m / 2 pi in turns per unit radius, float pair
-    float gmax0;         // largest |gap| per unit radius
     float g2;            // gamma / 2, high part (0 for padding)
     float l2;            // gamma / 2, low part
-    float R[6];          // real tail coefficients R1..R6, times gamma
-    float I[5];          // imaginary tail coefficients I0..I4, times gamma
+    float R[4];          // real tail coefficients R1..R4 (h_2..h_8), times gamma
+    float I[4];          // imaginary tail coefficients I0..I3 (h_3..h_9), times gamma
+    float R5, R6, I4;    // the h_10, h_12 and h_11 terms, times gamma
+    float gmax0;         // largest |gap| per unit radius
     // divided-difference branch, per unit radius: phase offsets of the two
     // first differences about the centroid (turns), their half gaps, and
     // 2 / (largest gap); the case (which vertex pair has the largest gap)
@@ -644,18 +651,21 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const float* __res
     o.R[1] = p2 * (1.0f / 720.0f);
     o.R[2] = -(p3 + q02) * (1.0f / 40320.0f);
     o.R[3] = fmaf(3.0f * q02, p0, p4) * (1.0f / 3628800.0f);
-    o.R[4] = -fmaf(6.0f * q02, p2, p4 * p0) * (1.0f / 479001600.0f);
-    o.R[5] = fmaf(10.0f * q02, p3, fmaf(p3, p3, q02 * q02)) * (1.0f / 87178291200.0f);
+    o.R5 = -fmaf(6.0f * q02, p2, p4 * p0) * (1.0f / 479001600.0f);
+    o.R6 = fmaf(10.0f * q02, p3, fmaf(p3, p3, q02 * q02)) * (1.0f / 87178291200.0f);
     o.I[0] = q0 * (1.0f / 120.0f);
     o.I[1] = -2.0f * q0 * p0 * (1.0f / 5040.0f);
     o.I[2] = 3.0f * q0 * p2 * (1.0f / 362880.0f);
     o.I[3] = -q0 * fmaf(4.0f, p3, q02) * (1.0f / 39916800.0f);
-    o.I[4] = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
+    o.I4 = q0 * fmaf(5.0f, p4, 4.0f * q02 * p0) * (1.0f / 6227020800.0f);
     // scaled by gamma (high part), so that the pair's tail comes out already
     // multiplied by gamma; the smallest scaled coefficients reach the float32
     // subnormal range only where their terms are far below the rounding of F
-    for (int k = 0; k < 6; ++k) o.R[k] *= t.gam;
-    for (int k = 0; k < 5; ++k) o.I[k] *= t.gam;
+    for (int k = 0; k < 4; ++k) o.R[k] *= t.gam;
+    for (int k = 0; k < 4; ++k) o.I[k] *= t.gam;
+    o.R5 *= t.gam;
+    o.R6 *= t.gam;
+    o.I4 *= t.gam;
     // largest gap: A = (a, c) with d2, B = (a, b) with d1, C = (b, c) with d3,
     // as in pair_mixed_divdiff
     const bool caseA = (a2 >= a1) && (a2 >= a3);
@@ -766,25 +776,83 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
     return h;
 }
 
+// Dithered centroid phase in turns of record t at the thread's q-th radius:
+// (rh + rlo)(dmh + dml) reduced mod 1, as the pair (tau, lo)
+__device__ __forceinline__ void radial_phase(const RadRec& t, const RadThread& h, int q, float& tau, float& lo)
+{
+    const float P = h.rh[q] * t.dmh;
+    const float e = fmaf(h.rh[q], t.dmh, -P);
+    lo = fmaf(h.rh[q], t.dml, fmaf(h.rlo[q], t.dmh, e));
+    tau = (P - rintf(P)) - h.dith[q];
+}
+
+// Taylor branch of record t at the thread's q-th radius: the tail as a
+// polynomial in rho = r^2, to h_12 or, when every gap is below DELTA_S, to h_9
+template <bool SHORT>
+__device__ __forceinline__ void radial_taylor(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
+                                              int q, float tau, float lo, float& fr, float& fi, float magic)
+{
+    const float rho = h.rho[q];
+    float ar, ai;
+    if (SHORT) {
+        ar = fmaf(fmaf(t.R[3], rho, t.R[2]), rho, t.R[1]);
+        ai = fmaf(fmaf(t.I[3], rho, t.I[2]), rho, t.I[1]);
+    } else {
+        ar = fmaf(fmaf(fmaf(fmaf(t.R6, rho, t.R5), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
+        ai = fmaf(fmaf(fmaf(t.I4, rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
+    }
+    ar = fmaf(fmaf(ar, rho, t.R[0]), rho, t.l2);
+    ai = fmaf(ai, rho, t.I[0]) * h.r3[q];
+    taylor_combine_half(tl, tau, lo, ar, ai, t.g2, fr, fi, magic);
+}
+
 // F_T of record t at the thread's q-th radius (dithered phase, Taylor branch
 // as a polynomial in r^2 or the largest-gap branch)
 __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
                                             int q, float& fr, float& fi, float magic)
 {
-    // dithered centroid phase in turns: (rh + rlo)(dmh + dml) reduced mod 1
-    const float P = h.rh[q] * t.dmh;
-    const float e = fmaf(h.rh[q], t.dmh, -P);
-    const float lo = fmaf(h.rh[q], t.dml, fmaf(h.rlo[q], t.dmh, e));
-    const float tau = (P - rintf(P)) - h.dith[q];
-    if (t.gmax0 < h.thr[q]) {
-        const float rho = h.rho[q];
-        float ar = fmaf(fmaf(fmaf(fmaf(t.R[5], rho, t.R[4]), rho, t.R[3]), rho, t.R[2]), rho, t.R[1]);
-        ar = fmaf(fmaf(ar, rho, t.R[0]), rho, t.l2);
-        float ai = fmaf(fmaf(fmaf(t.I[4], rho, t.I[3]), rho, t.I[2]), rho, t.I[1]);
-        ai = fmaf(ai, rho, t.I[0]) * h.r3[q];
-        taylor_combine_half(tl, tau, lo, ar, ai, t.g2, fr, fi, magic);
-    } else {
+    float tau, lo;
+    radial_phase(t, h, q, tau, lo);
+    if (t.gmax0 < h.thr[q])
+        radial_taylor<false>(tl, t, h, q, tau, lo, fr, fi, magic);
+    else
         radial_divdiff(tl, tau, lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
+}
+
+// One tile row of records at the thread's radii, in groups of 8 pairs
+// (float32 sums, dithered phases: random roundings), Kahan across groups.
+// VAR 0: per-pair branch choice; 1: every pair in the Taylor branch; 2: every
+// pair in the Taylor branch with all gaps below DELTA_S (short series).
+template <int VAR>
+__device__ __forceinline__ void radial_row(const TabEntry* __restrict__ tl, const RadRec* __restrict__ rec, int cnt8,
+                                           const RadThread& h, Kahan* kr, Kahan* ki)
+{
+    for (int j = 0; j < cnt8; j += 8) {
+        float br[WD_RAD_RPT], bi[WD_RAD_RPT];
+#pragma unroll
+        for (int q = 0; q < WD_RAD_RPT; ++q) br[q] = bi[q] = 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const RadRec& t = rec[j + jj];
+#pragma unroll
+            for (int q = 0; q < WD_RAD_RPT; ++q) {
+                float fr, fi;
+                if (VAR == 0) {
+                    radial_pair(tl, t, h, q, fr, fi, kMagic);
+                } else {
+                    float tau, lo;
+                    radial_phase(t, h, q, tau, lo);
+                    radial_taylor<VAR == 2>(tl, t, h, q, tau, lo, fr, fi, kMagic);
+                }
+                br[q] += fr;
+                bi[q] += fi;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < WD_RAD_RPT; ++q) {
+            kr[q].add(br[q]);
+            ki[q].add(bi[q]);
+        }
     }
 }
 
@@ -797,6 +865,17 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
                                            const float* __restrict__ dir, int64_t n_dir, const RadThread& h,
                                            double* acc_r, double* acc_i)
 {
+    static_assert(WD_RAD_TILE % 32 == 0 && WD_NPB % 32 == 0, "a warp builds records of one direction");
+    constexpr int kParts = WD_RAD_TILE / 32;                  // warps' worth of records per direction row
+    __shared__ unsigned int s_gmax[WD_RAD_ND * kParts];       // largest gmax0 per 32 records, as bits
+    __shared__ float s_rmax[WD_NPB / 32];                     // largest active radius per warp
+    {
+        float rm = 0.0f;
+#pragma unroll
+        for (int q = 0; q < WD_RAD_RPT; ++q) rm = fmaxf(rm, h.active[q] ? h.rh[q] : 0.0f);
+        const unsigned int u = __reduce_max_sync(0xffffffffu, __float_as_uint(rm));
+        if ((threadIdx.x & 31) == 0) s_rmax[threadIdx.x >> 5] = __uint_as_float(u);  // read after a barrier
+    }
     const TabEntry* tl = exp_table_lane(tab);
 #pragma unroll
     for (int q = 0; q < WD_RAD_RPT; ++q) acc_r[q] = acc_i[q] = 0.0;
@@ -804,50 +883,48 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
         const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
         const int cnt8 = (cnt + 7) & ~7;
         __syncthreads();
-        // records for WD_RAD_ND directions x cnt8 triangles (zero padding: gamma = 0)
+        // records for WD_RAD_ND directions x cnt8 triangles (zero padding:
+        // gamma = 0, gmax0 = 0), and the largest gmax0 of every 32 of them
+        // (gmax0 >= 0, so its bits order like its value)
         for (int i = threadIdx.x; i < WD_RAD_ND * WD_RAD_TILE; i += WD_NPB) {
             const int di = i / WD_RAD_TILE, j = i % WD_RAD_TILE;
             const int64_t dd = h.dg * WD_RAD_ND + di;
-            if (j >= cnt8) continue;
-            RadRec o;
-            if (j < cnt && dd < n_dir) {
-                const TriRecF tr = tris[tb + j];
-                make_radrec(tr, dir, n_dir, dd, o);
-            } else {
-                o = RadRec{};
+            float gm = 0.0f;
+            if (j < cnt8) {
+                RadRec o;
+                if (j < cnt && dd < n_dir) {
+                    const TriRecF tr = tris[tb + j];
+                    make_radrec(tr, dir, n_dir, dd, o);
+                } else {
+                    o = RadRec{};
+                }
+                gm = o.gmax0;
+                tile[di][j] = o;
             }
-            tile[di][j] = o;
+            const unsigned int wm = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
+            if ((threadIdx.x & 31) == 0) s_gmax[i / 32] = wm;
         }
         __syncthreads();
         if (!h.dir_ok) continue;  // warp-uniform
         const RadRec* rec = tile[h.dl];
-        // plain float32 sums over groups of 8 pairs (dithered phases: random
-        // roundings), Kahan across groups. No per-tile phase shift here: on
-        // ball rules the weight spreads over many nodes and the shift's
-        // float64 rotation cost 3% of the throughput without a measurable
-        // gain in accuracy (see the per-node kernel for the lattice case)
+        // No per-tile phase shift here: on ball rules the weight spreads over
+        // many nodes and the shift's float64 rotation cost 3% of the
+        // throughput without a measurable gain in accuracy (see the per-node
+        // kernel for the lattice case). Where every record of the row keeps
+        // every lane of the warp in the Taylor branch, the row runs without
+        // the per-pair branch test, and with the short series where every
+        // gap is below DELTA_S; the choice is the same for the whole warp.
+        unsigned int gu = 0u;
+#pragma unroll
+        for (int p = 0; p < kParts; ++p) gu = max(gu, s_gmax[h.dl * kParts + p]);
+        const float gap_row = __uint_as_float(gu) * s_rmax[threadIdx.x >> 5];  // bounds every lane's gaps
         Kahan kr[WD_RAD_RPT], ki[WD_RAD_RPT];
-        for (int j = 0; j < cnt8; j += 8) {
-            float br[WD_RAD_RPT], bi[WD_RAD_RPT];
-#pragma unroll
-            for (int q = 0; q < WD_RAD_RPT; ++q) br[q] = bi[q] = 0.0f;
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const RadRec& t = rec[j + jj];
-#pragma unroll
-                for (int q = 0; q < WD_RAD_RPT; ++q) {
-                    float fr, fi;
-                    radial_pair(tl, t, h, q, fr, fi, kMagic);
-                    br[q] += fr;
-                    bi[q] += fi;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < WD_RAD_RPT; ++q) {
-                kr[q].add(br[q]);
-                ki[q].add(bi[q]);
-            }
-        }
+        if (gap_row < kDeltaShort32)
+            radial_row<2>(tl, rec, cnt8, h, kr, ki);
+        else if (gap_row < kDelta32)
+            radial_row<1>(tl, rec, cnt8, h, kr, ki);
+        else
+            radial_row<0>(tl, rec, cnt8, h, kr, ki);
 #pragma unroll
         for (int q = 0; q < WD_RAD_RPT; ++q) {
             acc_r[q] += kr[q].value();
