@@ -41,8 +41,9 @@ N_MUFU_PER_PAIR = 6
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
 # DRAM bytes (read + write) of one mixed pair-kernel launch on the n = 64 sweep
 # query, from ncu (profiles/pair_kernel_radial_sweep_n64.md); None once the
-# kernel changes after that capture.
-PAIR_KERNEL_TRAFFIC_N64 = 48.70e6
+# kernel changes after that capture. The capture (48.70e6 bytes) predates the
+# whole-row Taylor variants, so it is not reported for the current kernel.
+PAIR_KERNEL_TRAFFIC_N64 = None
 
 
 def parse():
@@ -614,8 +615,9 @@ def main():
             "frac": pair_rate / peak,
             "traffic": PAIR_KERNEL_TRAFFIC_N64 if prec == wd.WD_MIXED else None,
             "traffic_note": "dram read+write bytes of the n=64 launch of pair_kernel_radial (ncu, "
-                            "profiles/pair_kernel_radial_sweep_n64.md); algorithmic bytes of that launch: W and nu^ "
-                            "per node (24 B x 1,769,472) + mesh records (64 B x 81,920) = 47.7 MB",
+                            "profiles/pair_kernel_radial_sweep_n64.md), null when the kernel changed after the "
+                            "capture; algorithmic bytes of that launch: W and nu^ per node (24 B x 1,769,472) + "
+                            "mesh records (64 B x 81,920) = 47.7 MB",
             "kernel": "pair_kernel_radial (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
             "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
                           % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
