@@ -98,9 +98,10 @@ __global__ void stage_kernel(const double* __restrict__ verts, int64_t nv,
 // ------------------------------------------------------------------ shared pieces
 // Taylor branch bounds: below a largest gap DELTA the centred phases satisfy
 // |y| <= 2 DELTA / 3. float64: DELTA = 1, series to n = 18 (remainder < 1e-18);
-// mixed: DELTA = 3, series to n = 12 (p <= 3, remainder < 3e-9); in the
+// mixed: DELTA = 3, series to n = 12 (p <= 3, remainder < 3.2e-9); in the
 // radial kernel also DELTA_S = 1.5 with the series to n = 9 (remainder
-// < 1e-9, the worst over sampled triangle shapes).
+// < 1.1e-9). Both bounds sum C(j+k, k) p^j |q|^k / (n+2)! over the dropped
+// n = 2j + 3k, with p <= DELTA^2 / 3 and |q| <= 2 (p/3)^(3/2).
 constexpr double kDelta64 = 1.0;
 constexpr int kTerms64 = 18;
 constexpr float kDelta32 = 3.0f;
