@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Throughput of the weak-distance hot path on B300: G triangle-frequency pairs/s.
 
-Default workload ("sweep"): icosahedral meshes n = 8, 16, 32, 64 (1,280 to
-81,920 triangles) against the unit sphere for s = 1 and s = 2, on the ball rule
-R = 128 with 192 radial x 96 polar x 192 azimuthal nodes and Hermitian halving
-(1,769,472 evaluated nodes). One step = the 8 distance queries, i.e. every
-(triangle, node) pair of every query: stage the mesh, evaluate the exact
-triangle transforms, sum per node, subtract the sphere, weight and reduce.
+Default workload ("large"): the icosahedral mesh n = 128 (327,680 triangles,
+vertices jittered radially by 1e-4, seed 7) against the unit sphere, s = 1, on
+the ball rule R = 256 with 256 radial x 128 polar x 256 azimuthal nodes and
+Hermitian halving (4,194,304 evaluated nodes, 1.37e12 pairs). One step = one
+distance query, i.e. every (triangle, node) pair: stage the mesh, evaluate the
+exact triangle transforms, sum per node, subtract the sphere, weight and
+reduce. The refinement sweep (n = 8..64, s = 1, 2, R = 128, 192 x 96 x 192
+Hermitian) is timed beside it, and every timed query's D is compared with the
+plain float64 path.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).
@@ -39,11 +42,14 @@ UNIT = "Gpair/s"
 N_FP32_PER_PAIR = 60
 N_MUFU_PER_PAIR = 6
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
-# DRAM bytes (read + write) of one mixed pair-kernel launch on the n = 64 sweep
-# query, from ncu (profiles/pair_kernel_radial_sweep_n64.md); None once the
-# kernel changes after that capture. The capture (48.70e6 bytes) predates the
-# whole-row Taylor variants, so it is not reported for the current kernel.
-PAIR_KERNEL_TRAFFIC_N64 = None
+# DRAM bytes (read + write) of one launch of the radial pair kernel on the
+# large query, from an ncu capture of the current kernel; None when the kernel
+# has changed since the capture.
+PAIR_KERNEL_TRAFFIC_LARGE = None
+# radial shells of the large rule whose D is recomputed in float64 after the
+# timed region (a 32-aligned window evaluates every node with the same float32
+# operations as the full launch)
+LARGE_CHECK_SHELLS = (0, 32)
 
 
 def parse():
@@ -52,19 +58,22 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["sweep", "large", "small"], default="sweep")
+    p.add_argument("--workload", choices=["large", "sweep", "small"], default="large")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-check", action="store_true", help="skip the mixed-vs-fp64 accuracy check")
+    p.add_argument("--no-sweep", action="store_true", help="skip the secondary refinement-sweep measurement")
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     p.add_argument("--only-n", type=int, default=None, help="restrict the sweep to one mesh (profiling runs)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-queries", type=int, default=2000)
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint batch and fitting measurement")
     p.add_argument("--no-paper", action="store_true", help="skip the paper's cube-rule refinement ladder")
-    p.add_argument("--case", choices=["adjoint-n16"], default=None,
-                   help="run one fixed case for a profiler and exit: three mixed gradients of the n=16 "
-                        "adjoint-configuration mesh (seed 0) on the 192x64x96 rule")
+    p.add_argument("--case", choices=["adjoint-n16", "large-window", "large"], default=None,
+                   help="run one fixed case for a profiler and exit: adjoint-n16 = three mixed gradients of the "
+                        "n=16 adjoint-configuration mesh (seed 0) on the 192x64x96 rule; large-window = two "
+                        "mixed distances of the large query on radial shells 128-159 of its rule; large = two "
+                        "mixed distances of the large query")
     return p.parse_args()
 
 
@@ -156,9 +165,86 @@ def measured_peaks():
         return {"sm_max_mhz": 2032.0}, "fallback"
 
 
-def pair_roofline_peak(sm_count, mhz):
-    clk_per_pair = max(N_FP32_PER_PAIR / 128.0, N_MUFU_PER_PAIR / 16.0)
+def pair_roofline_peak(sm_count, mhz, n_fp32=N_FP32_PER_PAIR):
+    clk_per_pair = max(n_fp32 / 128.0, N_MUFU_PER_PAIR / 16.0)
     return sm_count * mhz * 1e6 / clk_per_pair
+
+
+def fp64_distances(wd, ctx, rule, dv, dt, ss):
+    """D for each s in ss from one float64 transform of the mesh: the plain
+    float64 path (every pair, per-node sums and the weighted sum in float64)."""
+    import torch
+    n, _ = wd.wd_rule_info(rule)
+    xi, wg = wd.wd_rule_copy_nodes(rule)
+    re = torch.empty(n, dtype=torch.float64, device=dv.device)
+    im = torch.empty(n, dtype=torch.float64, device=dv.device)
+    wd.wd_mesh_ft_dev(ctx.handle, rule, dv, dt, wd.WD_FP64, re, im)
+    wd.wd_sync(ctx.handle)
+    delta = re.cpu().numpy() + 1j * im.cpu().numpy() - ctx.sphere_ft(rule)
+    r2 = (xi * xi).sum(1)
+    a2 = np.abs(delta) ** 2
+    return {s: float(np.sum(wg * (1.0 + r2) ** (-s) * a2)) for s in ss}
+
+
+def large_accuracy(wd, ctx, R, dv, dt, s, d_full):
+    """Mixed vs float64 D over radial shells LARGE_CHECK_SHELLS of the large
+    rule, through the timed entry point (the radial kernel)."""
+    import torch
+    win = ctx.rule_shells(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian, *LARGE_CHECK_SHELLS)
+    out = torch.zeros(1, dtype=torch.float64, device=dv.device)
+    wd.wd_distance_dev(ctx.handle, win, dv, dt, None, s, wd.WD_MIXED, out)
+    wd.wd_sync(ctx.handle)
+    dmx = out.item()
+    t0 = time.perf_counter()
+    d64 = fp64_distances(wd, ctx, win, dv, dt, (s,))[s]
+    return {"rel_err": (dmx - d64) / d64, "D_window_mixed": dmx, "D_window_fp64": d64,
+            "window_share_of_D": dmx / d_full, "fp64_seconds": time.perf_counter() - t0,
+            "shells": list(LARGE_CHECK_SHELLS), "n_r": R.n_r}
+
+
+def sweep_bench(wd, ctx, dev, stream, steps=2):
+    """The refinement sweep (8 queries) timed on the device after one warm-up
+    step, with every query's D compared with the float64 path."""
+    import torch
+    cfg, queries, R = workload("sweep")
+    rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+    n_eval, _ = wd.wd_rule_info(rule)
+    dq = [(torch.tensor(v, device=dev), torch.tensor(t, device=dev), s) for (v, t, s) in queries]
+    out = torch.zeros(len(dq), dtype=torch.float64, device=dev)
+    h = ctx.handle
+    for i, (v, t, s) in enumerate(dq):
+        wd.wd_distance_dev(h, rule, v, t, None, s, wd.WD_MIXED, out[i:i + 1], stream)
+    wd.wd_sync(h, stream)
+    q_ms = [0.0] * len(dq)
+    for _ in range(steps):
+        marks = []
+        for i, (v, t, s) in enumerate(dq):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            wd.wd_distance_dev(h, rule, v, t, None, s, wd.WD_MIXED, out[i:i + 1], stream)
+            e1.record(stream)
+            marks.append((e0, e1))
+        torch.cuda.synchronize()
+        for i, (e0, e1) in enumerate(marks):
+            q_ms[i] += e0.elapsed_time(e1) / steps
+    d_mixed = out.cpu().tolist()
+    pairs = [t.shape[0] * n_eval for (_, t, _) in dq]
+    per_query = []
+    t64 = time.perf_counter()
+    by_mesh = {}
+    for i, (v, t, s) in enumerate(dq):
+        key = t.shape[0]
+        if key not in by_mesh:
+            by_mesh[key] = fp64_distances(wd, ctx, rule, v, t, synth.SWEEP_SS)
+        d64 = by_mesh[key][s]
+        per_query.append({"n": int(round((t.shape[0] / 20) ** 0.5)), "s": s, "D_mixed": d_mixed[i], "D_fp64": d64,
+                          "rel_err": (d_mixed[i] - d64) / d64, "ms": q_ms[i],
+                          "gpairs_per_s": pairs[i] / q_ms[i] / 1e6})
+    return {"config": cfg, "gpairs_per_s": sum(pairs) / sum(q_ms) / 1e6, "steps": steps,
+            "queries": per_query, "max_abs_rel_err_vs_fp64": max(abs(q["rel_err"]) for q in per_query),
+            "queries_checked": len(per_query), "fp64_seconds": time.perf_counter() - t64,
+            "timing": "CUDA events per query on the launching stream after one warm-up step, mean of %d steps"
+                      % steps}
 
 
 def cpu_baseline(R, queries, seconds):
@@ -190,79 +276,111 @@ def cpu_baseline(R, queries, seconds):
                       "of the rule (%d nodes, %.3g pairs, %.1f s)" % (len(t), stride, len(idx), pairs, dt)}
 
 
+SERVE_PAIRS_PER_LAUNCH = 8_000_000_000
+
+
 def serve_bench(wd, ctx, n_queries, rate=500.0):
-    """Open-loop Poisson stream through the continuous-batching server (mixed),
-    against the plain one-query-per-launch float64 path on a sample."""
+    """Continuous batching (mixed) on the 2,000-query Poisson stream: capacity
+    (every query submitted at once), open-loop latency at the offered 500/s
+    and at 80 % of capacity; against the same queries run one per call in
+    mixed precision (host API, and device-resident through wd_distance_dev,
+    which gives the standalone kernel's pair rate) and in float64."""
+    import torch
     stream = synth.serve_stream(n_queries=n_queries, rate=rate, seed=0)
     rules = [(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian) for R in synth.SERVE_RULES.values()]
-    sv = wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, mem_cap_bytes=16 << 30, max_slots=64,
-                           max_pending=n_queries + 16, pairs_per_launch=4_000_000_000)
-    try:
-        for q in stream[:4]:  # warm-up: weight caches, first launches
-            wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
-        # service time: one query in flight at a time
-        svc = []
-        for q in stream[4:24]:
-            t0 = time.perf_counter()
-            wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
-            svc.append(1e3 * (time.perf_counter() - t0))
-        wd.wd_serve_stop(sv)
-        sv = wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, mem_cap_bytes=16 << 30, max_slots=64,
-                               max_pending=n_queries + 16, pairs_per_launch=4_000_000_000)
-        for q in stream[:4]:
-            wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
-        launches0 = ctx.launches()
+
+    def start(n):
+        return wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, mem_cap_bytes=16 << 30, max_slots=64,
+                                 max_pending=n + 16, pairs_per_launch=SERVE_PAIRS_PER_LAUNCH)
+
+    def open_loop(sv, qs):
         t_start = time.perf_counter()
         tickets = []
-        for q in stream:  # open loop: submit at the arrival times
+        for q in qs:  # submit at the arrival times
             delay = q.arrival_s - (time.perf_counter() - t_start)
             if delay > 0:
                 time.sleep(delay)
             tickets.append(wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R))
-        served = [wd.wd_serve_wait(sv, tk, 3600000) for tk in tickets]
-        st = wd.wd_serve_stats(sv)
-        wd.wd_serve_stop(sv)
-        # a second open-loop stream below capacity (80 % of the rate just achieved), so that
-        # the latency percentiles show the server rather than the queue of an overload
-        sub_rate = 0.8 * st["qps"]
-        n_sub = int(min(400, max(50, 10.0 * sub_rate)))
-        sub = synth.serve_stream(n_queries=n_sub, rate=sub_rate, seed=1)
-        sv = wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, mem_cap_bytes=16 << 30, max_slots=64,
-                               max_pending=n_sub + 16, pairs_per_launch=4_000_000_000)
-        for q in sub[:4]:
+        return [wd.wd_serve_wait(sv, tk, 3600000) for tk in tickets]
+
+    pairs_of = {R.R: R.n_eval() for R in synth.SERVE_RULES.values()}
+    total_pairs = sum(len(q.tris) * pairs_of[q.R] for q in stream)
+    res = {"queries": n_queries, "rules": ["R=%g %dx%dx%d%s" % (r[0], r[1], r[2], r[3], " herm" if r[4] else "")
+                                           for r in rules],
+           "pairs_per_launch": SERVE_PAIRS_PER_LAUNCH, "mean_pairs_per_query": total_pairs / len(stream)}
+    sv = start(n_queries)
+    try:
+        for q in stream[:4]:  # warm-up: weight caches
             wd.wd_serve_wait(sv, wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R), 600000)
-        t_start = time.perf_counter()
-        tk2 = []
-        for q in sub:
-            delay = q.arrival_s - (time.perf_counter() - t_start)
-            if delay > 0:
-                time.sleep(delay)
-            tk2.append(wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R))
-        for tk in tk2:
-            wd.wd_serve_wait(sv, tk, 3600000)
-        st2 = wd.wd_serve_stats(sv)
+        wd.wd_serve_stop(sv)
+        # capacity: the whole stream submitted at once
+        sv = start(n_queries)
+        t0 = time.perf_counter()
+        tks = [wd.wd_serve_submit(sv, q.verts, q.tris, q.s, q.R) for q in stream]
+        served = [wd.wd_serve_wait(sv, tk, 3600000) for tk in tks]
+        wall = time.perf_counter() - t0
+        st = wd.wd_serve_stats(sv)
+        busy = st["gpu_busy"] * (wall if st["qps"] <= 0 else st["completed"] / st["qps"])
+        res["capacity"] = {"qps": n_queries / wall, "seconds": wall, "launches": st["launches"],
+                           "gpu_busy": st["gpu_busy"], "serve_kernel_gpairs_per_s": total_pairs / busy / 1e9,
+                           "note": "all queries submitted at once; pair rate = pairs / device time of the launches"}
+        wd.wd_serve_stop(sv)
+        # open loop at the offered rate (above capacity: queueing dominates the latency)
+        sv = start(n_queries)
+        open_loop(sv, stream)
+        st = wd.wd_serve_stats(sv)
+        res["open_loop"] = {"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_us"] / 1e3,
+                            "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3, "gpu_busy": st["gpu_busy"],
+                            "launches": st["launches"], "note": "submit to result, queueing included"}
+        wd.wd_serve_stop(sv)
+        # open loop below capacity: the server's own latency
+        sub_rate = 0.8 * res["capacity"]["qps"]
+        n_sub = int(min(1000, max(100, 10.0 * sub_rate)))
+        sub = synth.serve_stream(n_queries=n_sub, rate=sub_rate, seed=1)
+        sv = start(n_sub)
+        open_loop(sv, sub)
+        st = wd.wd_serve_stats(sv)
+        res["below_capacity"] = {"queries": n_sub, "offered_qps": sub_rate, "achieved_qps": st["qps"],
+                                 "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                                 "max_ms": st["max_us"] / 1e3, "gpu_busy": st["gpu_busy"],
+                                 "note": "open loop at 80% of capacity, seed 1; submit to result"}
     finally:
         wd.wd_serve_stop(sv)
-    # plain float64 path, one query per call, on a sample of the stream
-    sample = stream[:6]
+    # baselines on the first queries of the same stream, one query per call
     rule_of = {R: ctx.rule(*next(r for r in rules if r[0] == R)) for R in synth.SERVE_RULES}
+    base = stream[:400]
     t0 = time.perf_counter()
-    ref = [ctx.distance(rule_of[q.R], q.verts, q.tris, None, q.s, wd.WD_FP64) for q in sample]
-    fp64_qps = len(sample) / (time.perf_counter() - t0)
-    errs = [abs(a - b) / b for a, b in zip(served[:len(sample)], ref)]
-    return {"queries": n_queries, "offered_qps": rate, "achieved_qps": st["qps"],
-            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
-            "latency_note": "open loop, submit to result, queueing included",
-            "service_ms_p50": statistics.median(svc), "service_ms_max": max(svc),
-            "fp64_one_per_launch_qps": fp64_qps, "speedup_vs_fp64_one_per_launch": st["qps"] / fp64_qps,
-            "max_rel_err_vs_fp64": max(errs), "fp64_sample": len(sample),
-            "launches": st["launches"], "gpu_kernel_launches": ctx.launches() - launches0,
-            "gpu_busy": st["gpu_busy"], "pairs": st["pairs"], "completed": st["completed"],
-            "rules": ["R=%g %dx%dx%d%s" % (r[0], r[1], r[2], r[3], " herm" if r[4] else "") for r in rules],
-            "below_capacity": {"queries": n_sub, "offered_qps": sub_rate, "achieved_qps": st2["qps"],
-                               "p50_ms": st2["p50_us"] / 1e3, "p99_ms": st2["p99_us"] / 1e3,
-                               "max_ms": st2["max_us"] / 1e3, "gpu_busy": st2["gpu_busy"],
-                               "note": "open loop at 80% of the achieved rate, seed 1; submit to result"}}
+    for q in base:
+        ctx.distance(rule_of[q.R], q.verts, q.tris, None, q.s, wd.WD_MIXED)
+    seq_qps = len(base) / (time.perf_counter() - t0)
+    dev = [(torch.tensor(q.verts, device="cuda"), torch.tensor(q.tris, device="cuda"), q) for q in base]
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for v, t, q in dev:
+        wd.wd_distance_dev(ctx.handle, rule_of[q.R], v, t, None, q.s, wd.WD_MIXED, out)
+    e1.record()
+    torch.cuda.synchronize()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    base_pairs = sum(len(q.tris) * pairs_of[q.R] for q in base)
+    fp = stream[:50]
+    t0 = time.perf_counter()
+    ref = [ctx.distance(rule_of[q.R], q.verts, q.tris, None, q.s, wd.WD_FP64) for q in fp]
+    fp64_qps = len(fp) / (time.perf_counter() - t0)
+    errs = [abs(a - b) / b for a, b in zip(served[:len(fp)], ref)]
+    res["baselines"] = {
+        "mixed_one_per_call_qps": seq_qps, "mixed_one_per_call_queries": len(base),
+        "mixed_one_per_call_note": "wd_distance (host meshes, synchronous) per query, same stream of queries",
+        "standalone_kernel_gpairs_per_s": base_pairs / dev_s / 1e9,
+        "standalone_note": "wd_distance_dev per query, meshes on the device, back to back (CUDA events)",
+        "fp64_one_per_call_qps": fp64_qps, "fp64_queries": len(fp)}
+    res["speedup_vs_mixed_one_per_call"] = res["capacity"]["qps"] / seq_qps
+    res["speedup_vs_fp64_one_per_call"] = res["capacity"]["qps"] / fp64_qps
+    res["serve_vs_standalone_pair_rate"] = (res["capacity"]["serve_kernel_gpairs_per_s"]
+                                            / res["baselines"]["standalone_kernel_gpairs_per_s"])
+    res["max_rel_err_vs_fp64"] = max(errs)
+    return res
 
 
 def adjoint_bench(wd, ctx):
@@ -326,7 +444,7 @@ def adjoint_bench(wd, ctx):
 
 
 def paper_bench(wd, ctx):
-    """The paper's own experiment (Sec. 4.2, Fig. 4b): icosahedral T_N,
+    """The paper's own experiment (Sec. 4.2, Fig. 3b): icosahedral T_N,
     N = 0..7, against the unit sphere in H_{-10} on the cube trapezoid rule
     xi_max = 5, M = 128 (paper's 2 pi convention, Hermitian half), mixed
     precision. Relative error = sqrt(D) / |sigma|, |sigma|^2 from the paper's
@@ -362,9 +480,9 @@ def paper_bench(wd, ctx):
         sec += ms / 1e3
     for a, b in zip(rows, rows[1:]):
         b["ratio_prev"] = a["rel_err"] / b["rel_err"]
-    # float64 path for N <= 6 (N = 7 alone would take about 100 s of float64 pairs)
+    # the plain float64 path at every level (N = 7: 3.5e11 float64 pairs, about 75 s)
     t64 = time.perf_counter()
-    for r in rows[:7]:
+    for r in rows:
         v, t = synth.icosphere_recursive(r["N"])
         r["D_fp64"] = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_FP64)
         r["mixed_vs_fp64"] = (r["D"] - r["D_fp64"]) / r["D_fp64"]
@@ -376,20 +494,19 @@ def paper_bench(wd, ctx):
             "s_paper": -synth.PAPER_S, "precision": "mixed",
             "sphere_norm2_rule_rel_err": abs(d_sphere - norm2) / norm2,
             "ladder": rows, "gpairs_per_s": pairs / sec / 1e9,
-            "paper_reference": "Fig. 4b: parallel to O(4^-N), about 1e-5 at N=7",
-            "fp64_seconds_N0_6": t64,
+            "paper_reference": "Fig. 3b: parallel to O(4^-N), about 1e-5 at N=7",
+            "fp64_seconds": t64, "max_abs_mixed_vs_fp64": max(abs(r["mixed_vs_fp64"]) for r in rows),
             "paper_timing_context": {
                 "paper_gpu_s_N7_M128": 0.94, "paper_gpu": "RTX A6000",
                 "paper_method": "8x8 Gauss-Legendre atoms + single-precision type-1 NUFFT (eps 1e-7), "
-                                "frequency-space reduction excluded (P:325)",
+                                "frequency-space reduction excluded (Sec. 4.3)",
                 "this_build_s_N7_M128": rows[7]["ms"] / 1e3,
                 "this_build_method": "exact triangle transform at all %.3g (triangle, node) pairs, mixed "
                                      "precision, reduction included" % (rows[7]["triangles"] * n_eval),
                 "prior_direct_method": "10 s on V100 for 100,000 triangles, M=100 (1.0e11 pairs) [IcDeTu2023]"},
             "accuracy_note": "D / |mu|^2 falls as 16^-N (2e-10 at N=7) and D is carried by the few thousand "
-                             "lowest-frequency nodes, so the mixed path's per-node rounding reaches D at "
-                             "~1e-6 by N=5 and grows about 16x per level; rel_err = sqrt(D)/|sigma| moves by "
-                             "half of that"}
+                             "nodes with |eta| < 1; the node blocks whose weight is within 1e-3 of the largest "
+                             "run the extended-precision pair form, the others plain float32 pairs"}
 
 
 def atoms_bench(wd, ctx):
@@ -476,6 +593,19 @@ def profile_case(name):
             wd.wd_distance_grad_dev(ctx.handle, rule, dv, dt, None, 1.0, wd.WD_MIXED, out, g)
         torch.cuda.synchronize()
         print("D %.12e |grad| %.12e" % (out.item(), g.norm().item()))
+    elif name in ("large-window", "large"):
+        R = synth.LARGE_RULE
+        if name == "large":
+            rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+        else:
+            rule = ctx.rule_shells(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian, 128, 160)
+        v, t = synth.large_mesh()
+        dv, dt = torch.tensor(v, device="cuda"), torch.tensor(t, device="cuda")
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            wd.wd_distance_dev(ctx.handle, rule, dv, dt, None, synth.LARGE_S, wd.WD_MIXED, out)
+        torch.cuda.synchronize()
+        print("D %.15e" % out.item())
     ctx.close()
 
 
@@ -568,18 +698,29 @@ def main():
     lat = sorted(q_ms)
     d_values = out.cpu().tolist()
 
-    # ---- accuracy of the mixed path against the float64 path (two smallest meshes)
+    # ---- accuracy of every timed query against the plain float64 path (after the timed region)
     accuracy = None
     if prec == wd.WD_MIXED and not args.no_check:
-        errs = []
-        for i, (v, t, s) in enumerate(dq):
-            if t.shape[0] > 6000:
-                continue
-            ref = torch.zeros(1, dtype=torch.float64, device=dev)
-            wd.wd_distance_dev(h, rule, v, t, None, s, wd.WD_FP64, ref, stream)
-            wd.wd_sync(h, stream)
-            errs.append(abs(d_values[i] - ref.item()) / ref.item())
-        accuracy = {"max_rel_err_vs_fp64": max(errs) if errs else None, "queries_checked": len(errs)}
+        if args.workload == "large":
+            v, t, s = dq[0]
+            acc = large_accuracy(wd, ctx, R, v, t, s, d_values[0])
+            accuracy = {"max_abs_rel_err_vs_fp64": abs(acc["rel_err"]), "queries_checked": len(dq),
+                        "within_1e-6": abs(acc["rel_err"]) <= 1e-6, "window": acc,
+                        "how": "D over radial shells %d-%d of %d of the timed rule through the timed entry point "
+                               "(a 32-aligned window evaluates every node with the same float32 operations as "
+                               "the full launch) against float64 D over the same nodes"
+                               % (LARGE_CHECK_SHELLS[0], LARGE_CHECK_SHELLS[1] - 1, R.n_r)}
+        else:
+            errs = []
+            by_mesh = {}
+            for i, (v, t, s) in enumerate(dq):
+                if t.shape[0] not in by_mesh:
+                    by_mesh[t.shape[0]] = fp64_distances(wd, ctx, rule, v, t, sorted({q[2] for q in dq}))
+                d64 = by_mesh[t.shape[0]][s]
+                errs.append((d_values[i] - d64) / d64)
+            accuracy = {"max_abs_rel_err_vs_fp64": max(abs(e) for e in errs), "rel_err": errs,
+                        "queries_checked": len(errs), "within_1e-6": max(abs(e) for e in errs) <= 1e-6,
+                        "how": "float64 D of every timed query from one float64 transform per mesh"}
 
     # ---- end to end through the host-buffer C-ABI call (pinned host inputs)
     pinned = []
@@ -611,28 +752,40 @@ def main():
     peaks, peak_src = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = pair_roofline_peak(sm_count, peaks.get("sm_max_mhz", 2032.0))
+    large = args.workload == "large" and prec == wd.WD_MIXED
     roof = {"bound": "alu", "achieved": pair_rate / 1e9, "peak": peak / 1e9, "unit": UNIT,
             "frac": pair_rate / peak,
-            "traffic": PAIR_KERNEL_TRAFFIC_N64 if prec == wd.WD_MIXED else None,
-            "traffic_note": "dram read+write bytes of the n=64 launch of pair_kernel_radial (ncu, "
-                            "profiles/pair_kernel_radial_sweep_n64.md), null when the kernel changed after the "
-                            "capture; algorithmic bytes of that launch: W and nu^ per node (24 B x 1,769,472) + "
-                            "mesh records (64 B x 81,920) = 47.7 MB",
+            "frac_at_45_fp32_ops": pair_rate / pair_roofline_peak(sm_count, peaks.get("sm_max_mhz", 2032.0), 45),
+            "traffic": PAIR_KERNEL_TRAFFIC_LARGE if large else None,
+            "traffic_note": "dram read+write bytes of one large-query launch of pair_kernel_radial from an ncu "
+                            "capture of the current kernel (null when the kernel changed after it); algorithmic "
+                            "bytes of that launch: W and nu^ per node (24 B x 4,194,304) + mesh records "
+                            "(64 B x 327,680) = 121.6 MB",
             "kernel": "pair_kernel_radial (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
             "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
                           % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
                              N_MUFU_PER_PAIR)}
     if prec == wd.WD_FP64:
         roof["note"] = "float64 path: bounded by the FP64 pipe, not by the FP32/MUFU roofline shown"
+    def section(run):
+        # a secondary measurement that fails is reported in the line, not fatal to it
+        try:
+            return run()
+        except Exception as exc:  # noqa: BLE001
+            return {"error": "%s: %s" % (type(exc).__name__, exc)}
+
+    sweep = None
+    if world == 1 and args.workload == "large" and prec == wd.WD_MIXED and not args.no_sweep:
+        sweep = section(lambda: sweep_bench(wd, ctx, dev, stream))
     serve = None
     if world == 1 and not args.no_serve and args.only_n is None:
-        serve = serve_bench(wd, ctx, args.serve_queries)
+        serve = section(lambda: serve_bench(wd, ctx, args.serve_queries))
     adjoint = None
     if world == 1 and not args.no_adjoint and args.only_n is None:
-        adjoint = adjoint_bench(wd, ctx)
+        adjoint = section(lambda: adjoint_bench(wd, ctx))
     paper = None
     if world == 1 and not args.no_paper and args.only_n is None:
-        paper = paper_bench(wd, ctx)
+        paper = section(lambda: paper_bench(wd, ctx))
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(R, queries, args.cpu_sample_seconds)
@@ -646,7 +799,8 @@ def main():
             "query_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                  "max": lat[-1], "note": "per-query kernel time, back-to-back queries"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "accuracy": accuracy, "distances": d_values[:len(dq)], "serve": serve, "adjoint": adjoint,
+            "accuracy": accuracy, "distances": d_values[:len(dq)], "sweep": sweep, "serve": serve,
+            "adjoint": adjoint,
             "paper": paper}
     print(json.dumps(line), flush=True)
     if dist:

@@ -121,6 +121,20 @@ typedef struct {
  * context; wd_rule_free is optional and only drops it from the cache. */
 wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* desc, wd_rule** out);
 
+/* The ball rule of `desc` restricted to its radial shells [shell_begin,
+ * shell_end) of the n_r Gauss-Legendre radii (0 <= shell_begin < shell_end <=
+ * n_r): the same nodes and weights as the full rule's nodes with those radial
+ * indices, in the same order. The quadrature is a sum over nodes, so D over
+ * windows that partition [0, n_r) adds up to D over the full rule; a window is
+ * the unit in which radial shells are split between calls, streams or GPUs
+ * (Sec. 3.2, rules over balls centred at the origin). The mixed path assigns
+ * every node the same phase dither as in the full rule, so for windows whose
+ * bounds are multiples of 32 each node's transform is evaluated with the same
+ * float32 operations as in the full rule. desc->kind must be WD_RULE_BALL.
+ * Cached like wd_build_freq_rule (by descriptor and window). */
+wd_status wd_build_freq_rule_shells(wd_ctx* ctx, const wd_rule_desc* desc, int shell_begin, int shell_end,
+                                    wd_rule** out);
+
 /* A rule from explicit host nodes: xi is SoA (x[n], y[n], z[n]), w_geom[n] the
  * s-free weights (the factor (1 + |xi|^2)^(-s) is applied per call). Used for
  * sub-rules and user rules. Not cached by descriptor; free with wd_rule_free. */
@@ -220,12 +234,17 @@ int64_t wd_launch_count(const wd_ctx* ctx);
 /* Continuous batching of distance queries (mesh vs the unit sphere) on one GPU.
  * Not in the paper, which times single evaluations (Sec. 4.3); this serves many
  * queries of uneven size at once. A worker thread admits queued queries while
- * request slots and a fixed device memory arena allow, and replays one captured
- * CUDA graph per launch: every launch evaluates a budget of (query, node-block)
- * items drawn round-robin from all admitted queries, so queries that arrive
- * while others run join the next launch and short ones are not held behind long
- * ones. Results equal those of wd_distance_dev with the same rule and precision
- * (same kernels, same summation order per node and per block). */
+ * request slots and a fixed device memory arena allow. Each admitted query gets
+ * the work plan of its own wd_distance_dev launch (node blocks x triangle
+ * chunks; chunks are capped at 8192 triangles so that a work item stays short).
+ * Every batched launch replays a captured CUDA graph over a budget of work
+ * items drawn round-robin from all admitted queries; a query's items may span
+ * launches, and its chunks, node blocks and final sum combine in its plan's
+ * fixed order. Queries that arrive while others run join the next launch, and
+ * the worker prepares launch k + 1 while launch k runs. Results are the same
+ * bits alone and in any mix, and equal those of wd_distance_dev with the same
+ * rule and precision whenever the chunk cap leaves the plan unchanged (within
+ * rounding of the chunk sums otherwise). */
 #define WD_SERVE_MAX_SLOTS 256
 
 typedef struct wd_server wd_server;
@@ -244,10 +263,10 @@ typedef struct {
 typedef struct {
     int64_t submitted, admitted, completed, rejected, timeouts, cancelled, failed, launches;
     int64_t pending, active, arena_used_bytes;
-    double pairs;              /* pairs evaluated */
+    double pairs;              /* (triangle, node) pairs of the queries completed */
     double p50_us, p99_us, max_us, mean_us;  /* submit-to-result latency of completed queries */
     double qps;                /* completed queries per second, first submit to last result */
-    double gpu_busy;           /* fraction of that span with a batched launch in flight */
+    double gpu_busy;           /* device time of the batched launches (events) over that span */
 } wd_serve_stats_t;
 
 /* Start the worker; builds the rules and captures the graph. */

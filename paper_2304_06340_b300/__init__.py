@@ -75,6 +75,8 @@ _sig("wd_destroy", [_vp], None)
 _sig("wd_last_error", [_vp], ctypes.c_char_p)
 _sig("wd_sync", [_vp, _vp])
 _sig("wd_build_freq_rule", [_vp, ctypes.POINTER(wd_rule_desc), ctypes.POINTER(_vp)])
+_sig("wd_build_freq_rule_shells", [_vp, ctypes.POINTER(wd_rule_desc), ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(_vp)])
 _sig("wd_rule_from_nodes", [_vp, _dp, _dp, _i64, ctypes.POINTER(_vp)])
 _sig("wd_rule_info", [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)])
 _sig("wd_rule_copy_nodes", [_vp, _dp, _dp])
@@ -192,6 +194,15 @@ def wd_build_freq_rule(ctx, R, n_r, n_polar, n_azim, hermitian=False, kind=WD_RU
     d = wd_rule_desc(int(kind), float(R), int(n_r), int(n_polar), int(n_azim), int(bool(hermitian)))
     h = _vp()
     _check(_lib.wd_build_freq_rule(ctx, ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def wd_build_freq_rule_shells(ctx, R, n_r, n_polar, n_azim, hermitian, shell_begin, shell_end):
+    """The ball rule (R, n_r, n_polar, n_azim) on its radial shells
+    [shell_begin, shell_end)."""
+    d = wd_rule_desc(WD_RULE_BALL, float(R), int(n_r), int(n_polar), int(n_azim), int(bool(hermitian)))
+    h = _vp()
+    _check(_lib.wd_build_freq_rule_shells(ctx, ctypes.byref(d), int(shell_begin), int(shell_end), ctypes.byref(h)))
     return h
 
 
@@ -401,6 +412,9 @@ class Context:
 
     def rule(self, R, n_r, n_polar, n_azim, hermitian=False):
         return wd_build_freq_rule(self.handle, R, n_r, n_polar, n_azim, hermitian)
+
+    def rule_shells(self, R, n_r, n_polar, n_azim, hermitian, shell_begin, shell_end):
+        return wd_build_freq_rule_shells(self.handle, R, n_r, n_polar, n_azim, hermitian, shell_begin, shell_end)
 
     def cube_rule(self, xi_max, M, hermitian=True):
         return wd_build_cube_rule(self.handle, xi_max, M, hermitian)

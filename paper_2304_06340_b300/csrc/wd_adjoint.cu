@@ -547,12 +547,12 @@ static_assert(sizeof(AdjRad) == 48, "AdjRad layout");
 // Residual rotated by the node's dither, direction-major: nd[d n_rad + ir] =
 // (Re, Im of r_k exp(2 pi i d_k), d_k, 0) for node k = ir n_dir + d.
 __global__ void adjoint_prep_radial(const double* __restrict__ resid, int n_rad, int64_t n_dir,
-                                    float4* __restrict__ nd)
+                                    int64_t dith_base, float4* __restrict__ nd)
 {
     const int64_t n = (int64_t)n_rad * n_dir;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ir = k / n_dir, d = k - ir * n_dir;
-        const float dith = node_dither(k);
+        const float dith = node_dither(dith_base + k);
         double sd, cd;
         sincospi(2.0 * (double)dith, &sd, &cd);
         const double r0 = resid[2 * k], r1 = resid[2 * k + 1];
@@ -934,22 +934,9 @@ __global__ void adjoint_scatter(const double* __restrict__ corner, const int32_t
 
 int resident_adjoint(wd_ctx* ctx, int precision, bool radial = false)
 {
-    static int cached[3][64] = {{0}};
-    const int m = radial ? 2 : (precision == WD_MIXED ? 1 : 0);
-    int& c = cached[m][ctx->device & 63];
-    if (c == 0) {
-        int per_sm = 0;
-        cudaError_t e =
-            m == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_radial, ADJ_TPB, 0)
-            : m == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_mixed, ADJ_TPB, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel_f64, ADJ_TPB, 0);
-        if (e != cudaSuccess || per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        c = per_sm * ctx->num_sms;
-    }
-    return c;
+    if (radial) return wd_resident(ctx, OCC_ADJOINT + 2, adjoint_kernel_radial, ADJ_TPB);
+    if (precision == WD_MIXED) return wd_resident(ctx, OCC_ADJOINT + 1, adjoint_kernel_mixed, ADJ_TPB);
+    return wd_resident(ctx, OCC_ADJOINT, adjoint_kernel_f64, ADJ_TPB);
 }
 
 }  // namespace
@@ -1025,7 +1012,8 @@ wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, con
         int64_t g = (n + 255) / 256;
         const int64_t cap = (int64_t)ctx->num_sms * 8;
         if (g > cap) g = cap;
-        adjoint_prep_radial<<<(int)g, 256, 0, st>>>(d_resid, rule->n_rad, rule->n_dir, nd);
+        adjoint_prep_radial<<<(int)g, 256, 0, st>>>(d_resid, rule->n_rad, rule->n_dir,
+                                                    (int64_t)rule->shell0 * rule->n_dir, nd);
         ctx->launches++;
         WD_CUDA(cudaGetLastError());
         adjoint_kernel_radial<<<plan.grid, ADJ_TPB, 0, st>>>(static_cast<const TriRecF*>(d_rec_mixed), nt, nd,

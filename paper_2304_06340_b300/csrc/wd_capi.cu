@@ -52,25 +52,48 @@ wd_status check_nu(const wd_measure* nu)
 }
 
 // Layout of one pair evaluation inside the context scratch, from offset `base`.
+// With a weight (s > 0) a mixed per-node plan also gets the rule's
+// extended-precision node blocks for s and room for their chunk partials.
 struct CoreLayout {
     PairPlan plan;
-    size_t rec = 0, partial = 0, blockD = 0, end = 0;
+    const PreciseSet* precise = nullptr;
+    size_t rec = 0, partial = 0, ppartial = 0, blockD = 0, end = 0;
 };
 
-CoreLayout core_layout(wd_ctx* ctx, const wd_rule* rule, int precision, int mode, int64_t n_rec, size_t base)
+wd_status core_layout(wd_ctx* ctx, wd_rule* rule, int precision, int mode, int64_t n_rec, size_t base, double s,
+                      CoreLayout* out)
 {
     CoreLayout L;
     const int64_t n_nodes = rule->n_eval;
     wd_plan_pair_rule(ctx, rule, precision, mode, n_rec, &L.plan);
+    if (precision == WD_MIXED && !L.plan.radial && mode != MODE_FT && s > 0.0 && L.plan.n_items > 0) {
+        wd_status st = wd_rule_precise(ctx, rule, s, &L.precise);
+        if (st != WD_OK) return st;
+        if (L.precise->n == 0) L.precise = nullptr;
+    }
     size_t off = align_up(base);
     L.rec = off;
     off += align_up((size_t)n_rec * wd_tri_record_bytes(precision));
     L.partial = off;
     if (L.plan.nchunks > 1) off += align_up((size_t)L.plan.nchunks * n_nodes * 2 * sizeof(double));
+    L.ppartial = off;
+    if (L.precise)
+        off += align_up(wd_precise_partial_bytes(wd_precise_plan(ctx, L.plan, L.precise->n, mode), L.precise->n));
     L.blockD = off;
     off += align_up((size_t)(L.plan.n_nb > 0 ? L.plan.n_nb : 1) * sizeof(double));
     L.end = off;
-    return L;
+    *out = L;
+    return WD_OK;
+}
+
+// the extended-precision blocks of a layout into the pair arguments
+void set_precise_args(wd_ctx* ctx, const CoreLayout& L, PairArgs& a)
+{
+    if (!L.precise) return;
+    a.precise_flag = L.precise->d_flag;
+    a.precise_list = L.precise->d_list;
+    a.n_precise = L.precise->n;
+    a.precise_partial = reinterpret_cast<double*>(ctx->ws + L.ppartial);
 }
 
 // Stage mu (and a mesh nu, negated) and run the pair kernel in `mode`.
@@ -99,6 +122,7 @@ wd_status run_core(wd_ctx* ctx, wd_rule* rule, const CoreLayout& L, int precisio
         if (r != WD_OK) return r;
     }
     a.partial = reinterpret_cast<double*>(ctx->ws + L.partial);
+    set_precise_args(ctx, L, a);
     a.cnt = ctx->d_counters;
     a.blockD = reinterpret_cast<double*>(ctx->ws + L.blockD);
     a.done = ctx->d_flags + 1;
@@ -265,7 +289,8 @@ extern "C" wd_status wd_mesh_ft_dev(wd_ctx* ctx, const wd_rule* rule_c, const do
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     wd_rule* rule = const_cast<wd_rule*>(rule_c);
     cudaStream_t s = (cudaStream_t)stream;
-    CoreLayout L = core_layout(ctx, rule, precision, MODE_FT, nt, 0);
+    CoreLayout L;
+    if ((st = core_layout(ctx, rule, precision, MODE_FT, nt, 0, 0.0, &L)) != WD_OK) return st;
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     return run_core(ctx, rule, L, precision, MODE_FT, d_verts, nv, d_tris, nt, nullptr, 0.0, d_re, d_im, s);
@@ -321,7 +346,8 @@ extern "C" wd_status wd_mesh_ft(wd_ctx* ctx, const wd_rule* rule_c, const wd_mes
     size_t ov = 0, ot = align_up(sizeof(double) * 3 * mesh->n_verts);
     size_t oo = ot + align_up(sizeof(int32_t) * 3 * mesh->n_tris);
     size_t base = oo + 2 * align_up(sizeof(double) * n);
-    CoreLayout L = core_layout(ctx, rule, precision, MODE_FT, mesh->n_tris, base);
+    CoreLayout L;
+    if ((st = core_layout(ctx, rule, precision, MODE_FT, mesh->n_tris, base, 0.0, &L)) != WD_OK) return st;
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     cudaStream_t s = 0;
@@ -393,7 +419,8 @@ extern "C" wd_status wd_distance_dev(wd_ctx* ctx, const wd_rule* rule_c, const d
     if ((st = wd_activate(ctx)) != WD_OK) return st;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     wd_rule* rule = const_cast<wd_rule*>(rule_c);
-    CoreLayout L = core_layout(ctx, rule, precision, MODE_DIST, nt + nt2, 0);
+    CoreLayout L;
+    if ((st = core_layout(ctx, rule, precision, MODE_DIST, nt + nt2, 0, s, &L)) != WD_OK) return st;
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     return run_core(ctx, rule, L, precision, MODE_DIST, d_verts, nv, d_tris, nt, nu, s, d_dist2, nullptr,
@@ -421,7 +448,8 @@ extern "C" wd_status wd_distance(wd_ctx* ctx, const wd_rule* rule_c, const wd_me
     size_t ov2 = ot + align_up(sizeof(int32_t) * 3 * mu->n_tris);
     size_t ot2 = ov2 + (m2 ? align_up(sizeof(double) * 3 * m2->n_verts) : 0);
     size_t base = ot2 + (m2 ? align_up(sizeof(int32_t) * 3 * m2->n_tris) : 0);
-    CoreLayout L = core_layout(ctx, rule, precision, MODE_DIST, mu->n_tris + nt2, base);
+    CoreLayout L;
+    if ((st = core_layout(ctx, rule, precision, MODE_DIST, mu->n_tris + nt2, base, s, &L)) != WD_OK) return st;
     if ((st = wd_ws_reserve(ctx, L.end)) != WD_OK) return st;
     if ((st = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st;
     cudaStream_t strm = 0;
@@ -454,12 +482,13 @@ struct GradLayout {
     size_t res = 0, rec64 = 0, adj = 0, sc = 0, rad = 0, end = 0;
 };
 
-static GradLayout grad_layout(wd_ctx* ctx, const wd_rule* rule, int precision, int64_t nt, int64_t nt2, int64_t nv,
-                              size_t base)
+static wd_status grad_layout(wd_ctx* ctx, wd_rule* rule, int precision, int64_t nt, int64_t nt2, int64_t nv,
+                             size_t base, double s, GradLayout* out)
 {
     GradLayout G;
     const int64_t n = rule->n_eval;
-    G.core = core_layout(ctx, rule, precision, MODE_RESID, nt + nt2, base);
+    wd_status st = core_layout(ctx, rule, precision, MODE_RESID, nt + nt2, base, s, &G.core);
+    if (st != WD_OK) return st;
     wd_plan_adjoint_rule(ctx, rule, precision, nt, &G.ap);
     size_t off = G.core.end;
     G.res = off;
@@ -473,7 +502,8 @@ static GradLayout grad_layout(wd_ctx* ctx, const wd_rule* rule, int precision, i
     G.rad = off;
     if (G.ap.radial) off += align_up(wd_adjoint_radial_bytes(rule));
     G.end = off;
-    return G;
+    *out = G;
+    return WD_OK;
 }
 
 // Gradient core on device pointers: forward pass in `precision` writing D and
@@ -485,10 +515,12 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
 {
     const int64_t nt2 = nu->kind == WD_NU_MESH ? nu->mesh->n_tris : 0;
     const int64_t n = rule->n_eval;
-    const GradLayout G = grad_layout(ctx, rule, precision, nt, nt2, nv, base);
+    GradLayout G;
+    wd_status st_ = grad_layout(ctx, rule, precision, nt, nt2, nv, base, s, &G);
+    if (st_ != WD_OK) return st_;
     const CoreLayout& L = G.core;
     const AdjPlan& ap = G.ap;
-    wd_status st_ = wd_ws_reserve(ctx, G.end);
+    st_ = wd_ws_reserve(ctx, G.end);
     if (st_ != WD_OK) return st_;
     if ((st_ = wd_counters_reserve(ctx, L.plan.n_nb)) != WD_OK) return st_;
     double* resid = reinterpret_cast<double*>(ctx->ws + G.res);
@@ -510,6 +542,7 @@ static wd_status grad_core(wd_ctx* ctx, wd_rule* rule, int precision, const doub
     }
     if ((st_ = wd_rule_weights(ctx, rule, s, &a.W, st)) != WD_OK) return st_;
     a.partial = reinterpret_cast<double*>(ctx->ws + L.partial);
+    set_precise_args(ctx, L, a);
     a.cnt = ctx->d_counters;
     a.blockD = reinterpret_cast<double*>(ctx->ws + L.blockD);
     a.done = ctx->d_flags + 1;
@@ -576,7 +609,9 @@ extern "C" wd_status wd_distance_grad(wd_ctx* ctx, const wd_rule* rule_c, const 
     cudaStream_t strm = 0;
     // grad_core reserves the scratch for its own layout, and a reallocation
     // there would lose the uploads; reserve that same layout before uploading
-    const GradLayout G = grad_layout(ctx, rule, precision, mu->n_tris, m2 ? m2->n_tris : 0, mu->n_verts, base);
+    GradLayout G;
+    if ((st = grad_layout(ctx, rule, precision, mu->n_tris, m2 ? m2->n_tris : 0, mu->n_verts, base, s, &G)) != WD_OK)
+        return st;
     if ((st = wd_ws_reserve(ctx, G.end)) != WD_OK) return st;
     if ((st = upload_mesh(ctx, mu, ov, ot, strm)) != WD_OK) return st;
     wd_mesh dm2{};

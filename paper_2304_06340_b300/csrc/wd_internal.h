@@ -73,6 +73,18 @@ struct __align__(16) TriRecF {
 };
 
 // ------------------------------------------------------------------ rule
+// Node blocks (WD_NPB consecutive nodes) of a rule that the mixed per-node
+// kernel evaluates in extended precision for one s: those holding a node whose
+// weight W_k = w_k (1 + c |xi_k|^2)^(-s) is at least kPreciseWeightFrac of the
+// largest. Where the weight is that concentrated, D rests on few nodes and
+// their float32 rounding does not average out.
+constexpr double kPreciseWeightFrac = 1e-3;
+struct PreciseSet {
+    int n = 0;                          // listed blocks
+    int* d_list = nullptr;              // their indices, ascending
+    unsigned char* d_flag = nullptr;    // per node block: 1 if listed
+};
+
 struct wd_rule {
     wd_ctx* ctx = nullptr;
     wd_rule_desc desc{};
@@ -86,12 +98,14 @@ struct wd_rule {
     double* d_wg = nullptr;
     double wscale = 1.0;              // W = w (1 + wscale |xi|^2)^(-s); 1/(4 pi^2) for cube rules
     // ball rules only: node k = rad[k / n_dir] * omega[k % n_dir] (radius outer)
+    int shell0 = 0, shell1 = 0;       // radial window [shell0, shell1) of the desc's n_r radii
     int n_rad = 0;
     int64_t n_dir = 0;
     double* d_rad = nullptr;          // radial nodes, n_rad
     float* d_dir = nullptr;           // per direction, SoA 9 * n_dir: omega (x, y, z) in float32,
                                       // then omega / 2 pi as float pairs: high (x, y, z), low (x, y, z)
     std::map<double, double*> w_cache;                  // s -> W_k
+    std::map<double, PreciseSet> precise_cache;         // s -> extended-precision node blocks
     std::map<std::array<double, 4>, double*> nu_cache;  // (radius, center) -> nu^ (re, im interleaved)
 };
 
@@ -111,7 +125,37 @@ struct wd_ctx {
     int* d_flags = nullptr;           // [0]: invalid-input flag, [1]: final-block counter
     double* d_scalar = nullptr;       // staging for host-variant scalar results
     std::atomic<int64_t> launches{0};
+    // resident blocks of each kernel on this context's device (0: not yet
+    // queried); written once per slot, any thread may fill a slot
+    std::atomic<int> occupancy[24] = {};
 };
+
+// resident-block slots of wd_ctx::occupancy
+enum OccSlot {
+    OCC_PAIR = 0,          // + 3 * mixed + mode (6 slots)
+    OCC_RADIAL = 6,        // + mode (3 slots)
+    OCC_SERVE = 9,         // + form, mixed per-node form at + 2 (3 slots)
+    OCC_ADJOINT = 12,      // + 0 float64, 1 mixed, 2 radial (3 slots)
+    OCC_PRECISE = 15,      // + mode (3 slots)
+    OCC_SERVE_PRECISE = 18,
+};
+// the cached count of slot `slot`, or query(kernel) * SMs stored there
+template <typename K>
+int wd_resident(wd_ctx* ctx, int slot, K kernel, int threads)
+{
+    int c = ctx->occupancy[slot].load(std::memory_order_relaxed);
+    if (c == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        c = per_sm * ctx->num_sms;
+        ctx->occupancy[slot].store(c, std::memory_order_relaxed);
+    }
+    return c;
+}
 
 // make ctx's device current
 wd_status wd_activate(wd_ctx* ctx);
@@ -123,6 +167,9 @@ wd_status wd_counters_reserve(wd_ctx* ctx, int64_t n);
 wd_status wd_rule_weights(wd_ctx* ctx, wd_rule* rule, double s, const double** d_w, cudaStream_t st);
 wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double* center,
                          const double** d_nu, cudaStream_t st);
+// the extended-precision node blocks of the mixed per-node plan for s (built
+// on the host and uploaded synchronously on first use, then cached)
+wd_status wd_rule_precise(wd_ctx* ctx, wd_rule* rule, double s, const PreciseSet** out);
 
 // ------------------------------------------------------------------ kernels
 enum PairMode { MODE_DIST = 0, MODE_FT = 1, MODE_RESID = 2 };
@@ -159,6 +206,13 @@ struct PairArgs {
     const float* dir = nullptr;
     int n_rad = 0;
     int64_t n_dir = 0;
+    int64_t dith_base = 0;        // radial plan: node index of the window's first node in the full rule
+    // mixed per-node plan: node blocks evaluated in extended precision (see
+    // wd_rule_precise), their chunk partials (wd_precise_partial_bytes)
+    const unsigned char* precise_flag = nullptr;  // per node block
+    const int* precise_list = nullptr;
+    int n_precise = 0;
+    double* precise_partial = nullptr;
 };
 
 constexpr int WD_NPB = 256;   // nodes per block: one node per thread
@@ -184,6 +238,13 @@ wd_status wd_plan_pair_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int
                             PairPlan* plan);
 // node arrays of a rule into the pair arguments (xi, n and, for ball rules, rad/dir)
 void wd_pair_args_rule(const wd_rule* rule, PairArgs& a);
+// the plan of the extended-precision kernel for n_precise listed blocks
+// (the plan's node blocks, triangle chunks of their own) and the bytes of its
+// chunk partials
+PairPlan wd_precise_plan(wd_ctx* ctx, const PairPlan& plan, int n_precise, int mode);
+size_t wd_precise_partial_bytes(const PairPlan& precise_plan, int n_precise);
+// launches the plan's kernel, then, for a mixed per-node plan with
+// args.n_precise > 0, the extended-precision kernel over the listed blocks
 wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
                          const PairArgs& args, cudaStream_t st);
 wd_status wd_launch_sphere(wd_ctx* ctx, const double* d_xi, int64_t n, double radius,
@@ -216,39 +277,38 @@ wd_status wd_launch_adjoint(wd_ctx* ctx, int precision, const AdjPlan& plan, con
                             void* d_radial, double* d_partial, void* d_scatter, const int32_t* d_tris, int64_t nv,
                             double* d_grad, cudaStream_t st);
 
-// batched serving kernel (wd_pair.cu), driven by a device descriptor table
+// batched serving kernels (wd_pair.cu), driven by a device descriptor table.
+// Every admitted request carries the arguments and the plan of its own
+// wd_distance launch (radial or per-node form); a launch runs contiguous
+// ranges of each request's work items, so a request's items may spread over
+// several launches and still sum in the order of its plan.
 struct ServeReq {
-    const void* rec;        // staged triangle records
-    int64_t T;              // records
-    const double* xi;       // rule nodes (SoA)
-    int64_t n;              // nodes
-    const double* W;        // weights for this request's s
-    const double* nu;       // sphere transform (re, im)
-    double* blockD;         // per-node-block partial sums of this request
-    const double* rad;      // mixed path, ball rule: radii and directions (wd_rule::d_dir layout; else null)
-    const float* dir;
-    int n_rad;
-    int n_rg;               // radius groups (node block nb = direction group * n_rg + radius group)
-    int64_t n_dir;
+    PairArgs a;             // out -> the request's result slot
+    PairPlan p;
+    PairPlan pp;            // mixed per-node plan: its extended-precision blocks (items after p's)
 };
-struct ServeItem {
-    int req;                // slot in the request table
-    int nb;                 // node block
+struct ServeRange {         // items [first, first + count) of request `req`
+    int req;
+    int count;
+    int64_t first;
+    int64_t start;          // launch-local index of the range's first item (prefix sum)
 };
-struct ServeFin {
-    int req;                // slot whose node blocks are all done after this launch
-    int n_nb;
-    int out;                // result index
-};
+enum { SERVE_RADIAL = 0, SERVE_NODE = 1, SERVE_PRECISE = 2, SERVE_FORMS = 3 };
 struct ServeTable {         // laid out in pinned host memory and copied whole per launch
-    int n_items;
-    int n_fin;
-    int pad[2];
+    int n_ranges[SERVE_FORMS];  // per kernel form
+    int pad0;
+    int64_t n_items[SERVE_FORMS];
+    int next[SERVE_FORMS];  // dynamic item counters (zero in the host copy)
+    int pad1;
 };
-wd_status wd_launch_serve(wd_ctx* ctx, int precision, int grid, const ServeTable* d_head,
-                          const ServeReq* d_reqs, const ServeItem* d_items, const ServeFin* d_fin,
-                          double* d_results, cudaStream_t st);
-int wd_serve_resident(wd_ctx* ctx, int precision);
+constexpr int WD_SERVE_RANGES = 512;  // ranges per form and launch
+// table layout: ServeTable, then WD_SERVE_RANGES ranges per form, then the requests
+wd_status wd_launch_serve(wd_ctx* ctx, int precision, ServeTable* d_head, const ServeRange* d_ranges,
+                          const ServeReq* d_reqs, cudaStream_t st);
+int wd_serve_resident(wd_ctx* ctx, int precision, int form);
+// the plan of a request: wd_plan_pair_rule's, with at most max_tiles tiles per item
+wd_status wd_plan_pair_serve(wd_ctx* ctx, const wd_rule* rule, int precision, int64_t n_tris, int max_tiles,
+                             PairPlan* plan);
 
 // Gauss-Legendre nodes and weights on [-1, 1], ascending (host, long double)
 void wd_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w);

@@ -326,6 +326,139 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
     pair_mixed_divdiff(tab, tau, tlo, g1, g2, t.gam, t.gam_lo, fr, fi, magic);
 }
 
+// ------------------------------------------------------------------ extended-precision per-node pair
+// On lattice rules with a steep weight (the paper's H_{-10}), D is carried by
+// a few thousand low-frequency nodes, where mu^ - nu^ is 1e-5 of mu^ and
+// every triangle's term has nearly the same phase: the float32 rounding of the
+// pairs, though independent across triangles, leaves each node's transform
+// about 2e-10 of its size off, which at so few nodes moves D by 1e-6 (Sec. 4.2
+// experiment at N = 6, 7). Node blocks that hold such nodes take this variant:
+// the centroid phase keeps the rounding errors of its mod-1 sums and of the
+// dither (two-sums), exp(-i theta) stays an unevaluated float pair (table
+// entry plus correction), gamma/2 times it is formed exactly, and the pairs
+// are summed with every rounding error kept. Per pair the relative error falls
+// from ~6e-8 to ~1e-9. The Taylor tail, O(p) of the leading 1/2, keeps float32
+// arithmetic, and the largest-gap branch (large |xi| h, where mu^ - nu^ is not
+// small) is the float32 one.
+
+// rounding error of s = fl(a + b): a + b = s + err exactly (Knuth's two-sum)
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float bb = s - a;
+    return (a - (s - bb)) + (b - bb);
+}
+
+// float32 sum carried as (s, c) with every addend's rounding error kept in c;
+// an addend's low part goes to c directly
+struct PairAcc {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float hi, float lo)
+    {
+        const float t = s + hi;
+        c += two_sum_err(s, hi, t) + lo;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// exp(-2 pi i tau) as float pairs: cos = ch + cl, -sin = sh + sl (expm_turns
+// without its last rounding: the table entry stays the high part)
+__device__ __forceinline__ void expm_turns_pair(const TabEntry* __restrict__ tl, float tau, float tlo, float& ch,
+                                                float& cl, float& sh, float& sl, float magic)
+{
+    const float km = fmaf(tau, (float)kTab, magic);
+    const int idx = __float_as_int(km) & (kTab - 1);
+    const float k = km - magic;
+    const float u = fmaf(-1.0f / kTab, k, tau);
+    const float xh = u * 6.28318548202514648f;
+    float xl = fmaf(u, 6.28318548202514648f, -xh);
+    xl = fmaf(u, -1.74845553e-7f, xl);
+    xl = fmaf(tlo, 6.28318548202514648f, xl);
+    const float x2 = xh * xh;
+    const float dc = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), -xh * xl);
+    const float ds = fmaf(xh * x2, -1.0f / 6.0f, xl);
+    const TabEntry t = tl[idx * kTabRep];
+    ch = t.ch;
+    cl = fmaf(t.ch, dc, fmaf(-t.sh, xh, fmaf(-t.sh, ds, t.cl)));
+    sh = -t.sh;
+    sl = -fmaf(t.sh, dc, fmaf(t.ch, xh, fmaf(t.ch, ds, t.sl)));
+}
+
+// F_T at node q as float pairs (frh + frl, fih + fil)
+__device__ __forceinline__ void pair_mixed_precise(const TabEntry* __restrict__ tab, const NodeF& q, const TriRecF& t,
+                                                   float& frh, float& frl, float& fih, float& fil, float magic)
+{
+    const float p0 = q.hx * t.mh[0], p1 = q.hy * t.mh[1], p2 = q.hz * t.mh[2];
+    const float a0 = p0 - rintf(p0), a1 = p1 - rintf(p1), a2 = p2 - rintf(p2);  // exact
+    float f = a0 + a1;
+    float lo = two_sum_err(a0, a1, f);
+    f -= rintf(f);
+    const float f2 = f + a2;
+    lo += two_sum_err(f, a2, f2);
+    f = f2 - rintf(f2);
+    const float tau = f - q.dith;
+    lo += two_sum_err(f, -q.dith, tau);
+    lo += fmaf(q.hx, t.mh[0], -p0) + fmaf(q.hy, t.mh[1], -p1) + fmaf(q.hz, t.mh[2], -p2);
+    lo = fmaf(q.hx, t.ml[0], lo);
+    lo = fmaf(q.hy, t.ml[1], lo);
+    lo = fmaf(q.hz, t.ml[2], lo);
+    lo = fmaf(q.lx, t.mh[0], lo);
+    lo = fmaf(q.ly, t.mh[1], lo);
+    lo = fmaf(q.lz, t.mh[2], lo);
+    const float g1 = fmaf(q.x, t.e1[0], fmaf(q.y, t.e1[1], q.z * t.e1[2]));
+    const float g2 = fmaf(q.x, t.e2[0], fmaf(q.y, t.e2[1], q.z * t.e2[2]));
+    const float g3 = g2 - g1;
+    const float gmax = fmaxf(fabsf(g1), fmaxf(fabsf(g2), fabsf(g3)));
+    if (gmax < kDelta32) {
+        // the tail Psi - 1/2 as in pair_mixed
+        const float ya = -(g1 + g2) * (1.0f / 3.0f);
+        const float yb = (2.0f * g1 - g2) * (1.0f / 3.0f);
+        const float yc = (2.0f * g2 - g1) * (1.0f / 3.0f);
+        const float p = (g1 * g1 - g1 * g2 + g2 * g2) * (1.0f / 3.0f);
+        const float qq = ya * yb * yc;
+        const float A = fmaf(g1, g1 - g2, g2 * g2);
+        const float q2 = qq * qq;
+        float re = fmaf(p, 1.0f / 87178291200.0f, -1.0f / 479001600.0f);
+        re = fmaf(re, p, 1.0f / 3628800.0f);
+        re = fmaf(re, p, -1.0f / 40320.0f);
+        re = fmaf(re, p, 1.0f / 720.0f);
+        float rq = fmaf(p, 10.0f / 87178291200.0f, -6.0f / 479001600.0f);
+        rq = fmaf(rq, p, 3.0f / 3628800.0f);
+        rq = fmaf(rq, p, -1.0f / 40320.0f);
+        rq = fmaf(q2, 1.0f / 87178291200.0f, rq);
+        float sr = fmaf(re, p * p, q2 * rq);
+        sr = fmaf(A, -1.388888899e-02f, fmaf(A, 1.034802868e-10f, sr));
+        float im = fmaf(p, 5.0f / 6227020800.0f, -4.0f / 39916800.0f);
+        im = fmaf(im, p, 3.0f / 362880.0f);
+        im = fmaf(im, p, -2.0f / 5040.0f);
+        im = fmaf(im, p, 1.0f / 120.0f);
+        const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
+        const float si = qq * fmaf(q2, iq, im);
+        float ch, cl, sh, sl;
+        expm_turns_pair(tab, tau, lo, ch, cl, sh, sl, magic);
+        // gamma (c + i s)(1/2 + sr + i si) with gamma/2 = g (exact) and the
+        // gamma-scaled tail ar + i ai (ar carries gamma_lo / 2): the product
+        // g ch exactly (high part and its error), g times the low parts, and
+        // the tail times the rounded c and s (the tail reaches 1/8 of 1/2 at
+        // gaps near DELTA, so it takes the whole of c and s)
+        const float g = 0.5f * t.gam;
+        const float ar = fmaf(t.gam, sr, 0.5f * t.gam_lo);
+        const float ai = t.gam * si;
+        const float c = ch + cl, sn = sh + sl;
+        frh = g * ch;
+        frl = fmaf(g, ch, -frh) + fmaf(g, cl, fmaf(c, ar, -sn * ai));
+        fih = g * sh;
+        fil = fmaf(g, sh, -fih) + fmaf(g, sl, fmaf(sn, ar, c * ai));
+        return;
+    }
+    float fr, fi;
+    pair_mixed_divdiff(tab, tau, lo, g1, g2, t.gam, t.gam_lo, fr, fi, magic);
+    frh = fr;
+    frl = 0.0f;
+    fih = fi;
+    fil = 0.0f;
+}
+
 // ------------------------------------------------------------------ block reduction
 __device__ __forceinline__ double block_sum(double v, double* red)
 {
@@ -370,10 +503,19 @@ __device__ __noinline__ double origin_transform(const TriRecF* __restrict__ rec,
 // D in fixed order (the last node block to finish adds the block sums).
 // ORIGIN: the node list may contain xi = 0 (not for ball rules: their radii
 // are Gauss-Legendre nodes inside (0, R)).
+// Chunk partial sums of a node: partial[2 (chunk * stride + slot)] (re, im).
+// The plain forms use slot = node and stride = n; the extended-precision
+// blocks have their own buffer, indexed by the block's place in their list.
+struct PartialSlots {
+    double* base;
+    int64_t stride;
+};
+
 template <bool MIXED, int MODE, int K, bool ORIGIN = true>
 __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan& p, int64_t nb, int chunk,
                                               const int64_t* node, const bool* active, const float* dith,
-                                              const double* acc_r, const double* acc_i, double* red, int& s_last)
+                                              const double* acc_r, const double* acc_i, double* red, int& s_last,
+                                              const PartialSlots& ps, const int64_t* slot)
 {
     const int64_t n = a.n;
     double mr[K], mi[K];
@@ -387,8 +529,8 @@ __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan&
 #pragma unroll
         for (int q = 0; q < K; ++q)
             if (active[q]) {
-                a.partial[2 * ((int64_t)chunk * n + node[q])] = acc_r[q];
-                a.partial[2 * ((int64_t)chunk * n + node[q]) + 1] = acc_i[q];
+                ps.base[2 * ((int64_t)chunk * ps.stride + slot[q])] = acc_r[q];
+                ps.base[2 * ((int64_t)chunk * ps.stride + slot[q]) + 1] = acc_i[q];
             }
         __threadfence();
         __syncthreads();
@@ -402,8 +544,8 @@ __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan&
             mi[q] = 0.0;
             if (active[q])
                 for (int c = 0; c < p.nchunks; ++c) {
-                    mr[q] += __ldcg(&a.partial[2 * ((int64_t)c * n + node[q])]);
-                    mi[q] += __ldcg(&a.partial[2 * ((int64_t)c * n + node[q]) + 1]);
+                    mr[q] += __ldcg(&ps.base[2 * ((int64_t)c * ps.stride + slot[q])]);
+                    mi[q] += __ldcg(&ps.base[2 * ((int64_t)c * ps.stride + slot[q]) + 1]);
                 }
         }
         if (threadIdx.x == 0) a.cnt[nb] = 0;  // ready for the next launch
@@ -481,94 +623,149 @@ __device__ __forceinline__ void node_epilogue(const PairArgs& a, const PairPlan&
 }
 
 // ------------------------------------------------------------------ pair kernel (a3..a7)
+// Shared memory of the per-node form: a tile of raw triangle records and the
+// exponential table (mixed path).
+template <bool MIXED>
+struct NodeSmem {
+    using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
+    Rec tile[WD_TILE];
+    TabEntry etab[MIXED ? kTab * kTabRep : 1];
+};
+
+// One work item (node block nb, triangle chunk) of the per-node form: one node
+// per thread, tiles of raw records, then the epilogue. Called by every thread
+// of the block (barriers inside); etab is filled. PRECISE: the
+// extended-precision pairs and sums (mixed only); its chunk partials live in
+// their own buffer at slot li * WD_NPB + thread, li the block's list index.
+template <bool MIXED, int MODE, bool PRECISE = false>
+__device__ __forceinline__ void pair_item(const PairArgs& a, const PairPlan& p, int64_t nb, int chunk, int64_t li,
+                                          NodeSmem<MIXED>& sm, double* red, int& s_last)
+{
+    static_assert(MIXED || !PRECISE, "the extended-precision variant is a mixed-path form");
+    using Rec = typename NodeSmem<MIXED>::Rec;
+    const int64_t n = a.n;
+    const int64_t node = nb * WD_NPB + threadIdx.x;
+    const bool active = node < n;
+    const double x = active ? a.xi[node] : 0.0;
+    const double y = active ? a.xi[n + node] : 0.0;
+    const double z = active ? a.xi[2 * n + node] : 0.0;
+
+    double acc_r = 0.0, acc_i = 0.0;
+    NodeD qd{x, y, z};
+    NodeF qf;
+    if (MIXED) {
+        const double inv2pi = 0.15915494309189533576888376337251;
+        const double X = x * inv2pi, Y = y * inv2pi, Z = z * inv2pi;
+        qf.x = (float)x;
+        qf.y = (float)y;
+        qf.z = (float)z;
+        qf.hx = (float)X;
+        qf.hy = (float)Y;
+        qf.hz = (float)Z;
+        qf.lx = (float)(X - (double)qf.hx);
+        qf.ly = (float)(Y - (double)qf.hy);
+        qf.lz = (float)(Z - (double)qf.hz);
+        qf.dith = node_dither(node);
+    }
+    const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
+    int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
+    if (t1 > a.T) t1 = a.T;
+    for (int64_t tb = t0; tb < t1; tb += WD_TILE) {
+        const int cnt = (int)((t1 - tb) < WD_TILE ? (t1 - tb) : WD_TILE);
+        __syncthreads();
+        // the mixed path reads the tile in groups of 4: pad with zero
+        // records, which contribute exactly zero (gamma = 0)
+        const int cnt4 = MIXED ? ((cnt + 3) & ~3) : cnt;
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(static_cast<const Rec*>(a.tris) + tb);
+            uint4* dst = reinterpret_cast<uint4*>(sm.tile);
+            const int nvec = cnt * (int)(sizeof(Rec) / 16);
+            const int nvec4 = cnt4 * (int)(sizeof(Rec) / 16);
+            for (int i = threadIdx.x; i < nvec4; i += WD_NPB)
+                dst[i] = i < nvec ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        if (PRECISE) {
+            const int shift = tile_shift(node, tb / WD_TILE);
+            const float magic = kMagic + (float)shift;
+            PairAcc kr, ki;
+            for (int j = 0; j < cnt4; j += 4) {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    float frh, frl, fih, fil;
+                    pair_mixed_precise(exp_table_lane(sm.etab), qf, reinterpret_cast<const TriRecF*>(sm.tile)[j + jj],
+                                       frh, frl, fih, fil, magic);
+                    kr.add(frh, frl);
+                    ki.add(fih, fil);
+                }
+            }
+            unshift_add(sm.etab, shift, kr.value(), ki.value(), acc_r, acc_i);
+        } else if (MIXED) {
+            // plain float32 sums over groups of 4 pairs (their phases are
+            // dithered, so the roundings are random), Kahan across groups;
+            // each tile with its own phase shift
+            const int shift = tile_shift(node, tb / WD_TILE);
+            const float magic = kMagic + (float)shift;
+            Kahan kr, ki;
+            for (int j = 0; j < cnt4; j += 4) {
+                float br = 0.0f, bi = 0.0f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    float fr, fi;
+                    pair_mixed(exp_table_lane(sm.etab), qf, reinterpret_cast<const TriRecF*>(sm.tile)[j + jj], fr,
+                               fi, magic);
+                    br += fr;
+                    bi += fi;
+                }
+                kr.add(br);
+                ki.add(bi);
+            }
+            unshift_add(sm.etab, shift, kr.value(), ki.value(), acc_r, acc_i);
+        } else {
+            for (int j = 0; j < cnt; ++j) {
+                double fr, fi;
+                pair_f64(qd, reinterpret_cast<const TriRecD*>(sm.tile)[j], fr, fi);
+                acc_r += fr;
+                acc_i += fi;
+            }
+        }
+    }
+
+    const float dith = MIXED ? qf.dith : 0.0f;
+    const PartialSlots ps{PRECISE ? a.precise_partial : a.partial, PRECISE ? (int64_t)a.n_precise * WD_NPB : a.n};
+    const int64_t slot = PRECISE ? li * WD_NPB + threadIdx.x : node;
+    node_epilogue<MIXED, MODE, 1>(a, p, nb, chunk, &node, &active, &dith, &acc_r, &acc_i, red, s_last, ps, &slot);
+}
+
+// The per-node form over every node block, skipping the blocks that the
+// extended-precision kernel takes (a.precise_flag, mixed path).
 template <bool MIXED, int MODE>
 __global__ void __launch_bounds__(WD_NPB) pair_kernel(const PairArgs a, const PairPlan p)
 {
-    using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
-    __shared__ __align__(16) Rec tile[WD_TILE];
+    __shared__ __align__(16) NodeSmem<MIXED> sm;
     __shared__ double red[WD_NPB / 32];
     __shared__ int s_last;
-    __shared__ TabEntry etab[kTab * kTabRep];
-    if (MIXED) fill_exp_table(etab);  // visible after the first tile barrier
-
-    const int64_t n = a.n;
+    if (MIXED) fill_exp_table(sm.etab);  // visible after the first tile barrier
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
         const int64_t nb = item / p.nchunks;
-        const int chunk = (int)(item - nb * p.nchunks);
-        const int64_t node = nb * WD_NPB + threadIdx.x;
-        const bool active = node < n;
-        const double x = active ? a.xi[node] : 0.0;
-        const double y = active ? a.xi[n + node] : 0.0;
-        const double z = active ? a.xi[2 * n + node] : 0.0;
+        if (MIXED && a.precise_flag && a.precise_flag[nb]) continue;  // block-uniform
+        pair_item<MIXED, MODE>(a, p, nb, (int)(item - nb * p.nchunks), 0, sm, red, s_last);
+    }
+}
 
-        double acc_r = 0.0, acc_i = 0.0;
-        NodeD qd{x, y, z};
-        NodeF qf;
-        if (MIXED) {
-            const double inv2pi = 0.15915494309189533576888376337251;
-            const double X = x * inv2pi, Y = y * inv2pi, Z = z * inv2pi;
-            qf.x = (float)x;
-            qf.y = (float)y;
-            qf.z = (float)z;
-            qf.hx = (float)X;
-            qf.hy = (float)Y;
-            qf.hz = (float)Z;
-            qf.lx = (float)(X - (double)qf.hx);
-            qf.ly = (float)(Y - (double)qf.hy);
-            qf.lz = (float)(Z - (double)qf.hz);
-            qf.dith = node_dither(node);
-        }
-        const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
-        int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
-        if (t1 > a.T) t1 = a.T;
-        for (int64_t tb = t0; tb < t1; tb += WD_TILE) {
-            const int cnt = (int)((t1 - tb) < WD_TILE ? (t1 - tb) : WD_TILE);
-            __syncthreads();
-            // the mixed path reads the tile in groups of 4: pad with zero
-            // records, which contribute exactly zero (gamma = 0)
-            const int cnt4 = MIXED ? ((cnt + 3) & ~3) : cnt;
-            {
-                const uint4* src = reinterpret_cast<const uint4*>(static_cast<const Rec*>(a.tris) + tb);
-                uint4* dst = reinterpret_cast<uint4*>(tile);
-                const int nvec = cnt * (int)(sizeof(Rec) / 16);
-                const int nvec4 = cnt4 * (int)(sizeof(Rec) / 16);
-                for (int i = threadIdx.x; i < nvec4; i += WD_NPB)
-                    dst[i] = i < nvec ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
-            }
-            __syncthreads();
-            if (MIXED) {
-                // plain float32 sums over groups of 4 pairs (their phases are
-                // dithered, so the roundings are random), Kahan across groups;
-                // each tile with its own phase shift
-                const int shift = tile_shift(node, tb / WD_TILE);
-                const float magic = kMagic + (float)shift;
-                Kahan kr, ki;
-                for (int j = 0; j < cnt4; j += 4) {
-                    float br = 0.0f, bi = 0.0f;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        float fr, fi;
-                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi,
-                                   magic);
-                        br += fr;
-                        bi += fi;
-                    }
-                    kr.add(br);
-                    ki.add(bi);
-                }
-                unshift_add(etab, shift, kr.value(), ki.value(), acc_r, acc_i);
-            } else {
-                for (int j = 0; j < cnt; ++j) {
-                    double fr, fi;
-                    pair_f64(qd, reinterpret_cast<const TriRecD*>(tile)[j], fr, fi);
-                    acc_r += fr;
-                    acc_i += fi;
-                }
-            }
-        }
-
-        const float dith = MIXED ? qf.dith : 0.0f;
-        node_epilogue<MIXED, MODE, 1>(a, p, nb, chunk, &node, &active, &dith, &acc_r, &acc_i, red, s_last);
+// The extended-precision blocks a.precise_list[0 .. n_precise), with the
+// triangle chunks of their own plan pp (more chunks: few blocks).
+template <int MODE>
+__global__ void __launch_bounds__(WD_NPB) pair_kernel_precise(const PairArgs a, const PairPlan pp)
+{
+    __shared__ __align__(16) NodeSmem<true> sm;
+    __shared__ double red[WD_NPB / 32];
+    __shared__ int s_last;
+    fill_exp_table(sm.etab);
+    const int64_t n_items = (int64_t)a.n_precise * pp.nchunks;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t li = item / pp.nchunks;
+        pair_item<true, MODE, true>(a, pp, a.precise_list[li], (int)(item - li * pp.nchunks), li, sm, red, s_last);
     }
 }
 
@@ -737,8 +934,10 @@ struct RadThread {
     float dith[WD_RAD_RPT];                  // the node's phase dither
 };
 
+// dith_base: index, in the full rule, of the first node of a radial window
+// (the dither is a function of that index, so a window's nodes keep theirs)
 __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ rad, int n_rad, int64_t n_dir,
-                                                   int64_t nb, int n_rg)
+                                                   int64_t nb, int n_rg, int64_t dith_base)
 {
     RadThread h;
     h.dl = threadIdx.x / WD_RAD_TPD;
@@ -759,7 +958,7 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
         h.r3[q] = (float)(r * r * r);
         h.thr[q] = h.active[q] ? (float)((double)kDelta32 / r) : 3.402823466e38f;
         h.rinv[q] = h.active[q] ? (float)(1.0 / r) : 0.0f;
-        h.dith[q] = node_dither(h.node[q]);
+        h.dith[q] = node_dither(dith_base + h.node[q]);
         // A warp holds 32 consecutive radii of one direction, and the branch
         // test r gmax0 < DELTA splits it wherever a record's seam falls inside
         // its radius range; the split warp then runs both branches. Where the
@@ -934,64 +1133,65 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
     }
 }
 
+struct RadSmem {
+    RadRec tile[WD_RAD_ND][WD_RAD_TILE];
+    TabEntry etab[kTab * kTabRep];
+};
+
+// One work item (radial node block nb, triangle chunk) of the radial form.
+// Called by every thread of the block (barriers inside); etab is filled.
+template <int MODE>
+__device__ __forceinline__ void radial_item(const PairArgs& a, const PairPlan& p, int64_t item, RadSmem& sm,
+                                            double* red, int& s_last)
+{
+    const int64_t nb = item / p.nchunks;
+    const int chunk = (int)(item - nb * p.nchunks);
+    const RadThread h = radial_thread(a.rad, a.n_rad, a.n_dir, nb, p.n_rg, a.dith_base);
+    const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
+    int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
+    if (t1 > a.T) t1 = a.T;
+    double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
+    radial_sum(sm.tile, sm.etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
+    const PartialSlots ps{a.partial, a.n};
+    node_epilogue<true, MODE, WD_RAD_RPT, false>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
+                                                 s_last, ps, h.node);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) pair_kernel_radial(const PairArgs a,
                                                                                       const PairPlan p)
 {
-    __shared__ __align__(16) RadRec tile[WD_RAD_ND][WD_RAD_TILE];
+    __shared__ __align__(16) RadSmem sm;
     __shared__ double red[WD_NPB / 32];
     __shared__ int s_last;
-    __shared__ TabEntry etab[kTab * kTabRep];
-    fill_exp_table(etab);  // visible after the first tile barrier
-    const TabEntry* tl = exp_table_lane(etab);
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-        const int64_t nb = item / p.nchunks;
-        const int chunk = (int)(item - nb * p.nchunks);
-        const RadThread h = radial_thread(a.rad, a.n_rad, a.n_dir, nb, p.n_rg);
-        const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
-        int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
-        if (t1 > a.T) t1 = a.T;
-        double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
-        radial_sum(tile, etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
-        node_epilogue<true, MODE, WD_RAD_RPT, false>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
-                                                     s_last);
-    }
+    fill_exp_table(sm.etab);  // visible after the first tile barrier
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x)
+        radial_item<MODE>(a, p, item, sm, red, s_last);
 }
 
 template <bool MIXED, int MODE>
 int resident_blocks(wd_ctx* ctx)
 {
-    static int cached[64] = {0};
-    int& c = cached[ctx->device & 63];
-    if (c == 0) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel<MIXED, MODE>, WD_NPB, 0) !=
-                cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        c = per_sm * ctx->num_sms;
-    }
-    return c;
+    return wd_resident(ctx, OCC_PAIR + 3 * (MIXED ? 1 : 0) + MODE, pair_kernel<MIXED, MODE>, WD_NPB);
+}
+
+template <int MODE>
+int resident_precise(wd_ctx* ctx)
+{
+    return wd_resident(ctx, OCC_PRECISE + MODE, pair_kernel_precise<MODE>, WD_NPB);
+}
+
+int resident_precise_for(wd_ctx* ctx, int mode)
+{
+    if (mode == MODE_FT) return resident_precise<MODE_FT>(ctx);
+    if (mode == MODE_RESID) return resident_precise<MODE_RESID>(ctx);
+    return resident_precise<MODE_DIST>(ctx);
 }
 
 template <int MODE>
 int resident_radial(wd_ctx* ctx)
 {
-    static int cached[64] = {0};
-    int& c = cached[ctx->device & 63];
-    if (c == 0) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel_radial<MODE>, WD_NPB, 0) !=
-                cudaSuccess ||
-            per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        c = per_sm * ctx->num_sms;
-    }
-    return c;
+    return wd_resident(ctx, OCC_RADIAL + MODE, pair_kernel_radial<MODE>, WD_NPB);
 }
 
 int resident_radial_for(wd_ctx* ctx, int mode)
@@ -1033,156 +1233,103 @@ int resident_for(wd_ctx* ctx, int precision, int mode)
     return resident_blocks<false, MODE_DIST>(ctx);
 }
 
-// ------------------------------------------------------------------ batched serving kernel
-// One work item = one node block (256 nodes) of one request, over all of that
-// request's triangles; the epilogue subtracts the sphere, weights and writes the
-// block's partial sum. Items of many requests run in the same launch, read from
-// a descriptor table in device memory. The summation order per node and per
-// block is the same as in pair_kernel with one triangle chunk, so a request's
-// result does not depend on what else is in the batch.
-template <bool MIXED>
-__global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel(const ServeTable* __restrict__ head,
-                                                       const ServeReq* __restrict__ reqs,
-                                                       const ServeItem* __restrict__ items)
+// ------------------------------------------------------------------ batched serving kernels
+// A launch of the serving loop runs work items of many requests. Each request
+// brings the arguments and plan of its own wd_distance launch; the table lists
+// contiguous ranges of its items (a range per request and launch). Blocks
+// take launch-local item indices from a counter, find their range (binary
+// search over the prefix sums) and run the same item body as pair_kernel or
+// pair_kernel_radial with the request's arguments. A request's node blocks
+// combine their triangle chunks and its final sum is formed in the fixed
+// order of its plan, by whichever launch finishes its last item, so the
+// result does not depend on what else shares the launches.
+__device__ __forceinline__ int64_t serve_next_item(int* counter, int* s_item)
 {
-    using Rec = typename std::conditional<MIXED, TriRecF, TriRecD>::type;
-    // per-node triangle tile or, for ball rules in the mixed path, the radial record tile
-    constexpr size_t kTileBytes = sizeof(Rec) * WD_TILE > sizeof(RadRec) * WD_RAD_ND * WD_RAD_TILE
-                                      ? sizeof(Rec) * WD_TILE
-                                      : sizeof(RadRec) * WD_RAD_ND * WD_RAD_TILE;
-    __shared__ __align__(16) unsigned char tbuf[kTileBytes];
-    Rec* tile = reinterpret_cast<Rec*>(tbuf);
+    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t it = *s_item;
+    __syncthreads();  // every thread has read s_item before it is written again
+    return it;
+}
+
+__device__ __forceinline__ const ServeRange& serve_find_range(const ServeRange* __restrict__ rg, int n, int64_t it)
+{
+    int lo = 0, hi = n - 1;  // largest r with rg[r].start <= it
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rg[mid].start <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return rg[lo];
+}
+
+__global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel_radial(
+    ServeTable* __restrict__ head, const ServeRange* __restrict__ ranges, const ServeReq* __restrict__ reqs)
+{
+    __shared__ __align__(16) RadSmem sm;
     __shared__ double red[WD_NPB / 32];
-    __shared__ TabEntry etab[MIXED ? kTab * kTabRep : 1];
-    if (MIXED) fill_exp_table(etab);
-    const int n_items = head->n_items;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const ServeItem item = items[it];
-        const ServeReq rq = reqs[item.req];
-        const int64_t n = rq.n;
-        if (MIXED && rq.rad) {  // block-uniform
-            const RadThread h = radial_thread(rq.rad, rq.n_rad, rq.n_dir, item.nb, rq.n_rg);
-            double mr[WD_RAD_RPT], mi[WD_RAD_RPT];
-            radial_sum(reinterpret_cast<RadRec(*)[WD_RAD_TILE]>(tbuf), etab, static_cast<const TriRecF*>(rq.rec), 0,
-                       rq.T, rq.dir, rq.n_dir, h, mr, mi);
-            double term = 0.0;
-#pragma unroll
-            for (int q = 0; q < WD_RAD_RPT; ++q) {
-                double sd, cd;
-                sincospi(2.0 * (double)h.dith[q], &sd, &cd);
-                const double r_ = mr[q] * cd + mi[q] * sd;
-                const double i_ = mi[q] * cd - mr[q] * sd;
-                if (h.active[q]) {
-                    const double dr = r_ - rq.nu[2 * h.node[q]], di = i_ - rq.nu[2 * h.node[q] + 1];
-                    term += rq.W[h.node[q]] * (dr * dr + di * di);
-                }
-            }
-            const double bsum = block_sum(term, red);
-            if (threadIdx.x == 0) rq.blockD[item.nb] = bsum;
-            continue;
-        }
-        const int64_t node = (int64_t)item.nb * WD_NPB + threadIdx.x;
-        const bool active = node < n;
-        const double x = active ? rq.xi[node] : 0.0;
-        const double y = active ? rq.xi[n + node] : 0.0;
-        const double z = active ? rq.xi[2 * n + node] : 0.0;
-        NodeD qd{x, y, z};
-        NodeF qf;
-        if (MIXED) {
-            const double inv2pi = 0.15915494309189533576888376337251;
-            const double X = x * inv2pi, Y = y * inv2pi, Z = z * inv2pi;
-            qf.x = (float)x;
-            qf.y = (float)y;
-            qf.z = (float)z;
-            qf.hx = (float)X;
-            qf.hy = (float)Y;
-            qf.hz = (float)Z;
-            qf.lx = (float)(X - (double)qf.hx);
-            qf.ly = (float)(Y - (double)qf.hy);
-            qf.lz = (float)(Z - (double)qf.hz);
-            qf.dith = node_dither(node);
-        }
-        double acc_r = 0.0, acc_i = 0.0;
-        for (int64_t tb = 0; tb < rq.T; tb += WD_TILE) {
-            const int cnt = (int)((rq.T - tb) < WD_TILE ? (rq.T - tb) : WD_TILE);
-            const int cnt4 = MIXED ? ((cnt + 3) & ~3) : cnt;
-            __syncthreads();
-            {
-                const uint4* src = reinterpret_cast<const uint4*>(static_cast<const Rec*>(rq.rec) + tb);
-                uint4* dst = reinterpret_cast<uint4*>(tile);
-                const int nvec = cnt * (int)(sizeof(Rec) / 16);
-                const int nvec4 = cnt4 * (int)(sizeof(Rec) / 16);
-                for (int i = threadIdx.x; i < nvec4; i += WD_NPB)
-                    dst[i] = i < nvec ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
-            }
-            __syncthreads();
-            if (MIXED) {
-                const int shift = tile_shift(node, tb / WD_TILE);
-                const float magic = kMagic + (float)shift;
-                Kahan kr, ki;
-                for (int j = 0; j < cnt4; j += 4) {
-                    float br = 0.0f, bi = 0.0f;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        float fr, fi;
-                        pair_mixed(exp_table_lane(etab), qf, reinterpret_cast<const TriRecF*>(tile)[j + jj], fr, fi,
-                                   magic);
-                        br += fr;
-                        bi += fi;
-                    }
-                    kr.add(br);
-                    ki.add(bi);
-                }
-                unshift_add(etab, shift, kr.value(), ki.value(), acc_r, acc_i);
-            } else {
-                for (int j = 0; j < cnt; ++j) {
-                    double fr, fi;
-                    pair_f64(qd, reinterpret_cast<const TriRecD*>(tile)[j], fr, fi);
-                    acc_r += fr;
-                    acc_i += fi;
-                }
-            }
-        }
-        double mr = acc_r, mi = acc_i;
-        if (MIXED) {
-            double sd, cd;
-            sincospi(2.0 * (double)qf.dith, &sd, &cd);
-            const double r_ = mr * cd + mi * sd;
-            mi = mi * cd - mr * sd;
-            mr = r_;
-            const bool origin = active && x == 0.0 && y == 0.0 && z == 0.0;
-            if (__syncthreads_or(origin)) {
-                const double m0 = origin_transform(static_cast<const TriRecF*>(rq.rec), rq.T, red);
-                if (origin) {
-                    mr = m0;
-                    mi = 0.0;
-                }
-            }
-        }
-        double term = 0.0;
-        if (active) {
-            const double dr = mr - rq.nu[2 * node], di = mi - rq.nu[2 * node + 1];
-            term = rq.W[node] * (dr * dr + di * di);
-        }
-        const double bsum = block_sum(term, red);
-        if (threadIdx.x == 0) rq.blockD[item.nb] = bsum;
+    __shared__ int s_last, s_item;
+    const int64_t n_items = head->n_items[SERVE_RADIAL];
+    if (n_items == 0) return;
+    fill_exp_table(sm.etab);  // visible after the first tile barrier
+    const int n_rg = head->n_ranges[SERVE_RADIAL];
+    for (;;) {
+        const int64_t it = serve_next_item(&head->next[SERVE_RADIAL], &s_item);
+        if (it >= n_items) break;
+        const ServeRange& r = serve_find_range(ranges, n_rg, it);
+        const ServeReq& rq = reqs[r.req];
+        radial_item<MODE_DIST>(rq.a, rq.p, r.first + (it - r.start), sm, red, s_last);
     }
 }
 
-// Fixed-order sum of the block partials of every request that completes in
-// this launch (one block per request).
-__global__ void serve_finalize(const ServeTable* __restrict__ head, const ServeReq* __restrict__ reqs,
-                               const ServeFin* __restrict__ fin, double* __restrict__ results)
+template <bool MIXED>
+__global__ void __launch_bounds__(WD_NPB) serve_kernel_node(ServeTable* __restrict__ head,
+                                                            const ServeRange* __restrict__ ranges,
+                                                            const ServeReq* __restrict__ reqs)
 {
+    __shared__ __align__(16) NodeSmem<MIXED> sm;
     __shared__ double red[WD_NPB / 32];
-    for (int f = blockIdx.x; f < head->n_fin; f += gridDim.x) {
-        const ServeFin e = fin[f];
-        const double* bd = reqs[e.req].blockD;
-        double v = 0.0;
-        for (int i = threadIdx.x; i < e.n_nb; i += WD_NPB) v += bd[i];
-        const double tot = block_sum(v, red);
-        if (threadIdx.x == 0) results[e.out] = tot;
-        __syncthreads();
+    __shared__ int s_last, s_item;
+    const int64_t n_items = head->n_items[SERVE_NODE];
+    if (n_items == 0) return;
+    if (MIXED) fill_exp_table(sm.etab);
+    const ServeRange* rg = ranges + WD_SERVE_RANGES;
+    const int n_rg = head->n_ranges[SERVE_NODE];
+    for (;;) {
+        const int64_t it = serve_next_item(&head->next[SERVE_NODE], &s_item);
+        if (it >= n_items) break;
+        const ServeRange& r = serve_find_range(rg, n_rg, it);
+        const ServeReq& rq = reqs[r.req];
+        const int64_t item = r.first + (it - r.start);
+        const int64_t nb = item / rq.p.nchunks;
+        if (MIXED && rq.a.precise_flag && rq.a.precise_flag[nb]) continue;  // the precise form's block
+        pair_item<MIXED, MODE_DIST>(rq.a, rq.p, nb, (int)(item - nb * rq.p.nchunks), 0, sm, red, s_last);
+    }
+}
+
+// The extended-precision blocks of requests with a mixed per-node plan: item
+// i of a request is chunk i mod pp.nchunks of its listed block i / pp.nchunks.
+__global__ void __launch_bounds__(WD_NPB) serve_kernel_precise(ServeTable* __restrict__ head,
+                                                               const ServeRange* __restrict__ ranges,
+                                                               const ServeReq* __restrict__ reqs)
+{
+    __shared__ __align__(16) NodeSmem<true> sm;
+    __shared__ double red[WD_NPB / 32];
+    __shared__ int s_last, s_item;
+    const int64_t n_items = head->n_items[SERVE_PRECISE];
+    if (n_items == 0) return;
+    fill_exp_table(sm.etab);
+    const ServeRange* rg = ranges + 2 * WD_SERVE_RANGES;
+    const int n_rg = head->n_ranges[SERVE_PRECISE];
+    for (;;) {
+        const int64_t it = serve_next_item(&head->next[SERVE_PRECISE], &s_item);
+        if (it >= n_items) break;
+        const ServeRange& r = serve_find_range(rg, n_rg, it);
+        const ServeReq& rq = reqs[r.req];
+        const int64_t item = r.first + (it - r.start);
+        const int64_t li = item / rq.pp.nchunks;
+        pair_item<true, MODE_DIST, true>(rq.a, rq.pp, rq.a.precise_list[li], (int)(item - li * rq.pp.nchunks), li,
+                                         sm, red, s_last);
     }
 }
 
@@ -1241,6 +1388,31 @@ wd_status wd_plan_pair_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int
     return WD_OK;
 }
 
+PairPlan wd_precise_plan(wd_ctx* ctx, const PairPlan& plan, int n_precise, int mode)
+{
+    PairPlan q = plan;
+    const int64_t resident = resident_precise_for(ctx, mode);
+    const int64_t target = 4 * resident;
+    int64_t nch = 1;
+    if (n_precise > 0 && n_precise < target && q.n_tiles > 1) {
+        nch = (target + n_precise - 1) / n_precise;
+        if (nch > q.n_tiles) nch = q.n_tiles;
+    }
+    const int64_t tpc = q.n_tiles > 0 ? (q.n_tiles + nch - 1) / nch : 0;
+    if (tpc > 0) nch = (q.n_tiles + tpc - 1) / tpc;
+    if (nch < 1) nch = 1;
+    q.tiles_per_chunk = (int)tpc;
+    q.nchunks = (int)nch;
+    q.n_items = (int64_t)n_precise * nch;
+    q.grid = (int)(q.n_items < resident ? q.n_items : resident);
+    return q;
+}
+
+size_t wd_precise_partial_bytes(const PairPlan& pp, int n_precise)
+{
+    return pp.nchunks > 1 ? sizeof(double) * 2 * (size_t)pp.nchunks * (size_t)n_precise * WD_NPB : 0;
+}
+
 void wd_pair_args_rule(const wd_rule* rule, PairArgs& a)
 {
     a.xi = rule->d_xi;
@@ -1249,6 +1421,7 @@ void wd_pair_args_rule(const wd_rule* rule, PairArgs& a)
     a.dir = rule->d_dir;
     a.n_rad = rule->n_rad;
     a.n_dir = rule->n_dir;
+    a.dith_base = (int64_t)rule->shell0 * rule->n_dir;
 }
 
 wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
@@ -1267,6 +1440,18 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
         if (mode == MODE_FT) pair_kernel<true, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else if (mode == MODE_RESID) pair_kernel<true, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else pair_kernel<true, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        if (args.n_precise > 0) {
+            WD_CUDA(cudaGetLastError());
+            ctx->launches++;
+            const PairPlan pp = wd_precise_plan(ctx, plan, args.n_precise, mode);
+            if (pp.nchunks > 1 && !args.precise_partial) {
+                wd_set_error("internal: extended-precision blocks without their partial buffer");
+                return WD_EINVAL;
+            }
+            if (mode == MODE_FT) pair_kernel_precise<MODE_FT><<<pp.grid, WD_NPB, 0, st>>>(args, pp);
+            else if (mode == MODE_RESID) pair_kernel_precise<MODE_RESID><<<pp.grid, WD_NPB, 0, st>>>(args, pp);
+            else pair_kernel_precise<MODE_DIST><<<pp.grid, WD_NPB, 0, st>>>(args, pp);
+        }
     } else {
         if (mode == MODE_FT) pair_kernel<false, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else if (mode == MODE_RESID) pair_kernel<false, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
@@ -1277,33 +1462,46 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
     return WD_OK;
 }
 
-int wd_serve_resident(wd_ctx* ctx, int precision)
+int wd_serve_resident(wd_ctx* ctx, int precision, int form)
 {
-    static int cached[2][64] = {{0}};
-    int& c = cached[precision == WD_MIXED ? 1 : 0][ctx->device & 63];
-    if (c == 0) {
-        int per_sm = 0;
-        cudaError_t e = precision == WD_MIXED
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel<true>, WD_NPB, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel<false>, WD_NPB, 0);
-        if (e != cudaSuccess || per_sm < 1) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        c = per_sm * ctx->num_sms;
-    }
-    return c;
+    if (form == SERVE_RADIAL) return wd_resident(ctx, OCC_SERVE, serve_kernel_radial, WD_NPB);
+    if (form == SERVE_PRECISE) return wd_resident(ctx, OCC_SERVE_PRECISE, serve_kernel_precise, WD_NPB);
+    return precision == WD_MIXED ? wd_resident(ctx, OCC_SERVE + 2, serve_kernel_node<true>, WD_NPB)
+                                 : wd_resident(ctx, OCC_SERVE + 1, serve_kernel_node<false>, WD_NPB);
 }
 
-wd_status wd_launch_serve(wd_ctx* ctx, int precision, int grid, const ServeTable* d_head,
-                          const ServeReq* d_reqs, const ServeItem* d_items, const ServeFin* d_fin,
-                          double* d_results, cudaStream_t st)
+wd_status wd_plan_pair_serve(wd_ctx* ctx, const wd_rule* rule, int precision, int64_t n_tris, int max_tiles,
+                             PairPlan* plan)
 {
-    if (precision == WD_MIXED) serve_kernel<true><<<grid, WD_NPB, 0, st>>>(d_head, d_reqs, d_items);
-    else serve_kernel<false><<<grid, WD_NPB, 0, st>>>(d_head, d_reqs, d_items);
+    PairPlan p;
+    wd_status st = wd_plan_pair_rule(ctx, rule, precision, MODE_DIST, n_tris, &p);
+    if (st != WD_OK) return st;
+    if (max_tiles >= 1 && p.tiles_per_chunk > max_tiles) {
+        p.tiles_per_chunk = max_tiles;
+        p.nchunks = (int)((p.n_tiles + max_tiles - 1) / max_tiles);
+        p.n_items = p.n_nb * p.nchunks;
+    }
+    *plan = p;
+    return WD_OK;
+}
+
+wd_status wd_launch_serve(wd_ctx* ctx, int precision, ServeTable* d_head, const ServeRange* d_ranges,
+                          const ServeReq* d_reqs, cudaStream_t st)
+{
+    if (precision == WD_MIXED) {
+        serve_kernel_radial<<<wd_serve_resident(ctx, precision, SERVE_RADIAL), WD_NPB, 0, st>>>(d_head, d_ranges,
+                                                                                              d_reqs);
+        WD_CUDA(cudaGetLastError());
+        serve_kernel_node<true><<<wd_serve_resident(ctx, precision, SERVE_NODE), WD_NPB, 0, st>>>(d_head, d_ranges,
+                                                                                                d_reqs);
+        WD_CUDA(cudaGetLastError());
+        serve_kernel_precise<<<wd_serve_resident(ctx, precision, SERVE_PRECISE), WD_NPB, 0, st>>>(d_head, d_ranges,
+                                                                                                d_reqs);
+    } else {
+        serve_kernel_node<false><<<wd_serve_resident(ctx, precision, SERVE_NODE), WD_NPB, 0, st>>>(d_head, d_ranges,
+                                                                                                 d_reqs);
+    }
     WD_CUDA(cudaGetLastError());
-    serve_finalize<<<ctx->num_sms, WD_NPB, 0, st>>>(d_head, d_reqs, d_fin, d_results);
-    WD_CUDA(cudaGetLastError());
-    ctx->launches += 2;
+    ctx->launches += precision == WD_MIXED ? 3 : 1;
     return WD_OK;
 }

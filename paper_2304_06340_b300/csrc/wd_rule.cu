@@ -1,5 +1,6 @@
 // Frequency rules (Sec. 3.2) and the per-rule device caches: the s-dependent
 // weights and the reference sphere's transform (Eq. (ft_nsphere_sinc)).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -126,6 +127,10 @@ void release_rule(wd_rule* r)
     cudaFree(r->d_rad);
     cudaFree(r->d_dir);
     for (auto& kv : r->w_cache) cudaFree(kv.second);
+    for (auto& kv : r->precise_cache) {
+        cudaFree(kv.second.d_list);
+        cudaFree(kv.second.d_flag);
+    }
     for (auto& kv : r->nu_cache) cudaFree(kv.second);
     delete r;
 }
@@ -224,6 +229,56 @@ wd_status wd_rule_sphere(wd_ctx* ctx, wd_rule* rule, double radius, const double
     return settle_cache_fill(st);
 }
 
+wd_status wd_rule_precise(wd_ctx* ctx, wd_rule* rule, double s, const PreciseSet** out)
+{
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    auto it = rule->precise_cache.find(s);
+    if (it != rule->precise_cache.end()) {
+        *out = &it->second;
+        return WD_OK;
+    }
+    // the weights in float64 on the host, from the rule's host copy; the
+    // choice only has to be deterministic, not bitwise the device's weights
+    const int64_t n = rule->n_eval;
+    const int64_t n_nb = (n + WD_NPB - 1) / WD_NPB;
+    std::vector<double> W(n);
+    double wmax = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const double x = rule->h_xi[k], y = rule->h_xi[n + k], z = rule->h_xi[2 * n + k];
+        W[k] = std::fabs(rule->h_wg[k]) * std::exp(-s * std::log1p(rule->wscale * (x * x + y * y + z * z)));
+        wmax = std::max(wmax, W[k]);
+    }
+    std::vector<unsigned char> flag(n_nb > 0 ? n_nb : 1, 0);
+    std::vector<int> list;
+    for (int64_t b = 0; b < n_nb; ++b) {
+        bool hit = false;
+        for (int64_t k = b * WD_NPB; k < std::min(n, (b + 1) * WD_NPB) && !hit; ++k)
+            hit = W[k] >= kPreciseWeightFrac * wmax;
+        if (hit) {
+            flag[b] = 1;
+            list.push_back((int)b);
+        }
+    }
+    PreciseSet ps;
+    ps.n = (int)list.size();
+    if (ps.n > 0) {
+        if (wd_dev_alloc(&ps.d_flag, flag.size(), "precise-block flags") != cudaSuccess ||
+            wd_dev_alloc(&ps.d_list, sizeof(int) * list.size(), "precise-block list") != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ps.d_flag);
+            cudaFree(ps.d_list);
+            wd_set_error("out of device memory for the extended-precision block list");
+            return WD_ENOMEM;
+        }
+        WD_CUDA(cudaMemcpy(ps.d_flag, flag.data(), flag.size(), cudaMemcpyHostToDevice));
+        WD_CUDA(cudaMemcpy(ps.d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
+    }
+    wd_log(4, "rule %p, s=%g: %d of %lld node blocks in extended precision", (void*)rule, s, ps.n, (long long)n_nb);
+    auto ins = rule->precise_cache.emplace(s, ps).first;
+    *out = &ins->second;
+    return WD_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 // The paper's cube trapezoid rule (Sec. 3.2), nodes at xi = 2 pi eta: see
 // WD_RULE_CUBE_TRAP in wd.h. Built in long double like the ball rule.
@@ -284,23 +339,27 @@ static wd_status build_cube_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** o
     return WD_OK;
 }
 
-extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** out)
+// The ball rule (Sec. 3.2, rules over balls centred at the origin) on its
+// radial shells [s0, s1): Gauss-Legendre radii on [0, R] with the r^2
+// Jacobian, Gauss-Legendre u = cos(theta), trapezoid phi. [0, n_r) is the
+// full rule.
+static wd_status build_ball_rule(wd_ctx* ctx, const wd_rule_desc* d, int s0, int s1, wd_rule** out)
 {
-    WdRange nvtx_range("wd_build_freq_rule");
-    WD_CHECK(ctx && d && out, WD_EINVAL, "null argument");
-    if (d->kind == WD_RULE_CUBE_TRAP) return build_cube_rule(ctx, d, out);
     WD_CHECK(d->kind == WD_RULE_BALL, WD_EINVAL, "rule kind must be WD_RULE_BALL or WD_RULE_CUBE_TRAP");
     WD_CHECK(std::isfinite(d->R) && d->R > 0.0, WD_EINVAL, "R must be finite and > 0");
     WD_CHECK(d->n_r >= 1 && d->n_polar >= 1 && d->n_azim >= 1, WD_EINVAL, "node counts must be >= 1");
     WD_CHECK(!d->hermitian || d->n_polar % 2 == 0, WD_EINVAL,
              "hermitian halving needs an even polar node count");
-    int64_t n_total = (int64_t)d->n_r * d->n_polar * d->n_azim;
-    WD_CHECK(n_total <= (int64_t)1 << 31, WD_EINVAL, "rule too large (more than 2^31 nodes)");
+    WD_CHECK(s0 >= 0 && s0 < s1 && s1 <= d->n_r, WD_EINVAL,
+             "radial shell window must satisfy 0 <= shell_begin < shell_end <= n_r");
+    int64_t n_total = (int64_t)(s1 - s0) * d->n_polar * d->n_azim;
+    WD_CHECK((int64_t)d->n_r * d->n_polar * d->n_azim <= (int64_t)1 << 31, WD_EINVAL,
+             "rule too large (more than 2^31 nodes)");
     wd_status st = wd_activate(ctx);
     if (st != WD_OK) return st;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     for (wd_rule* r : ctx->rules)
-        if (same_desc(r->desc, *d)) {
+        if (same_desc(r->desc, *d) && r->shell0 == s0 && r->shell1 == s1) {
             *out = r;
             return WD_OK;
         }
@@ -314,7 +373,9 @@ extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_r
     r->desc.hermitian = d->hermitian ? 1 : 0;
     r->cached = true;
     r->n_total = n_total;
-    r->n_eval = (int64_t)d->n_r * n_u * d->n_azim;
+    r->n_eval = (int64_t)(s1 - s0) * n_u * d->n_azim;
+    r->shell0 = s0;
+    r->shell1 = s1;
     const int64_t n = r->n_eval;
     r->h_xi.resize(3 * n);
     r->h_wg.resize(n);
@@ -327,11 +388,11 @@ extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_r
     const long double w_phi = 2.0L * kPi / d->n_azim;
     const long double half_R = 0.5L * (long double)d->R;
     // the same nodes factored as radius x unit direction, for the radial kernel
-    r->n_rad = d->n_r;
+    r->n_rad = s1 - s0;
     r->n_dir = (int64_t)n_u * d->n_azim;
-    r->h_rad.resize(d->n_r);
+    r->h_rad.resize(r->n_rad);
     r->h_dir.resize(9 * r->n_dir);
-    for (int i = 0; i < d->n_r; ++i) r->h_rad[i] = (double)(half_R * (1.0L + xr[i]));
+    for (int i = s0; i < s1; ++i) r->h_rad[i - s0] = (double)(half_R * (1.0L + xr[i]));
     for (int j = 0, kd = 0; j < n_u; ++j) {
         const long double u = xu[u0 + j], sn = sqrtl(1.0L - u * u);
         for (int m = 0; m < d->n_azim; ++m, ++kd) {
@@ -346,7 +407,7 @@ extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_r
         }
     }
     int64_t k = 0;
-    for (int i = 0; i < d->n_r; ++i) {
+    for (int i = s0; i < s1; ++i) {
         long double rr = half_R * (1.0L + xr[i]);
         long double w_r = half_R * wr[i] * rr * rr;  // Jacobian r^2 of spherical coordinates
         for (int j = 0; j < n_u; ++j) {
@@ -369,6 +430,23 @@ extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_r
     ctx->rules.push_back(r);
     *out = r;
     return WD_OK;
+}
+
+extern "C" wd_status wd_build_freq_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** out)
+{
+    WdRange nvtx_range("wd_build_freq_rule");
+    WD_CHECK(ctx && d && out, WD_EINVAL, "null argument");
+    if (d->kind == WD_RULE_CUBE_TRAP) return build_cube_rule(ctx, d, out);
+    return build_ball_rule(ctx, d, 0, d->n_r, out);
+}
+
+extern "C" wd_status wd_build_freq_rule_shells(wd_ctx* ctx, const wd_rule_desc* d, int shell_begin, int shell_end,
+                                               wd_rule** out)
+{
+    WdRange nvtx_range("wd_build_freq_rule_shells");
+    WD_CHECK(ctx && d && out, WD_EINVAL, "null argument");
+    WD_CHECK(d->kind == WD_RULE_BALL, WD_EINVAL, "radial shell windows exist for ball rules only");
+    return build_ball_rule(ctx, d, shell_begin, shell_end, out);
 }
 
 extern "C" wd_status wd_rule_from_nodes(wd_ctx* ctx, const double* xi, const double* w_geom,

@@ -2,14 +2,19 @@
 //
 // submit() copies a query (mesh, s, R) into host memory and queues it. A worker
 // thread admits queued queries while request slots and device memory (a fixed
-// arena, first-fit) are free, stages their meshes, and then repeatedly replays
-// one captured CUDA graph: copy the descriptor table from pinned memory, run
-// the batched pair kernel over a budget of (request, node block) items drawn
-// round-robin from every admitted query, sum the blocks of the queries that
-// finished, and copy their results back. Queries that arrive while a launch is
-// running join the next one, so short and long queries share the device and a
-// long query never holds back the short ones. The frequency rules, their
-// weights and the sphere's transform stay resident on the device.
+// arena, first-fit) are free, stages their meshes, and gives each the plan of
+// its own wd_distance launch: node blocks x triangle chunks, chunks capped so
+// that one work item stays short. Each batched launch replays a captured CUDA
+// graph that copies a descriptor table from pinned memory, runs the batched
+// pair kernels over contiguous ranges of the admitted queries' work items
+// (a share of a pair budget per query, round-robin, largest items first) and
+// copies the result slots back. Blocks take items from a counter. A query's
+// chunks, node blocks and final sum combine in the fixed order of its plan in
+// whichever launch runs its last item, so results do not depend on the mix.
+// Two tables alternate: the worker builds and enqueues launch k + 1 while
+// launch k runs, then retires the queries that launch k finished. Queries that
+// arrive meanwhile join the next launch; the frequency rules, their weights
+// and the sphere's transform stay resident on the device.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -17,6 +22,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -28,8 +34,9 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kMaxSlots = WD_SERVE_MAX_SLOTS;
-constexpr int kMaxItems = 1 << 17;
-constexpr int kRoundRobinBlocks = 8;  // node blocks taken per request per round
+constexpr int kRoundItems = 8;    // work items taken per query per round-robin round
+constexpr int kMaxItemTiles = 64; // triangle tiles per work item (2^21 pairs of a 256-node block)
+constexpr int kBuffers = 2;       // launch tables in flight
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -48,11 +55,23 @@ struct Request {
     wd_status status = WD_OK;
     double result = 0.0;
     bool cancel = false;
+    std::string why;            // failure reason, for wd_last_error of the waiting client
     // device side
     size_t off = 0, bytes = 0;
     int slot = -1;
-    int n_nb = 0, next_nb = 0;
-    bool staged = false;
+    PairPlan plan;
+    const PreciseSet* precise = nullptr;  // mixed per-node plan: extended-precision blocks for s
+    PairPlan pplan;             // their plan; their items follow plan's
+    int64_t n_items = 0;        // plan.n_items (+ pplan.n_items)
+    int64_t next_item = 0;      // first item not yet given to a launch
+    int64_t last_seq = -1;      // last launch that runs items of this query
+    int64_t finish_seq = -1;    // the launch that runs its last item (result valid once it completes)
+};
+
+// Arena layout of one request: records, chunk partials, block sums, counters
+// (node blocks, then the final-block counter), vertices, triangles.
+struct ReqLayout {
+    size_t rec = 0, partial = 0, ppartial = 0, blockD = 0, cnt = 0, done = 0, verts = 0, tris = 0, end = 0;
 };
 
 // First-fit allocator over one device arena.
@@ -125,34 +144,54 @@ struct wd_server {
     Arena arena;
     char* d_arena = nullptr;
     std::vector<RuleEntry> rules;
-    // descriptor table: pinned host copy and device copy with the same layout
-    size_t table_bytes = 0, off_reqs = 0, off_items = 0, off_fin = 0;
-    char* h_table = nullptr;
-    char* d_table = nullptr;
-    double* h_results = nullptr;
+    // descriptor tables: per buffer a pinned host copy and a device copy with
+    // the same layout (ServeTable, ranges of both forms, request descriptors)
+    size_t table_bytes = 0, off_ranges = 0, off_reqs = 0;
+    char* h_table[kBuffers] = {nullptr, nullptr};
+    char* d_table[kBuffers] = {nullptr, nullptr};
+    double* h_results[kBuffers] = {nullptr, nullptr};
     double* d_results = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int grid = 0;
+    cudaGraphExec_t graph[kBuffers] = {nullptr, nullptr};
+    cudaEvent_t ev_start[kBuffers] = {nullptr, nullptr}, ev_end[kBuffers] = {nullptr, nullptr};
+    int kernels_per_launch = 0;
     // statistics
     wd_serve_stats_t st{};
     std::vector<double> lat_us;
     Clock::time_point t_first_submit{}, t_last_done{};
     bool any_submit = false;
-    double busy_s = 0.0;
+    double busy_s = 0.0;          // device time of completed launches (events)
     wd_status fatal = WD_OK;
+    std::string fatal_msg;
     int drop_nth = 0;        // WD_FAULT_DROP_COMPLETION at start (0: off)
     int64_t n_ok_seen = 0;   // successful completions so far
 };
 
 namespace {
 
-size_t request_bytes(const wd_server* sv, const Request* r)
+ReqLayout request_layout(const wd_server* sv, const Request* r)
 {
     const int64_t T = (int64_t)r->tris.size() / 3;
     const int64_t V = (int64_t)r->verts.size() / 3;
-    return align_up(wd_tri_record_bytes(sv->cfg.precision) * (size_t)(T > 0 ? T : 1)) +
-           align_up(sizeof(double) * (size_t)(r->n_nb > 0 ? r->n_nb : 1)) +
-           align_up(sizeof(double) * 3 * (size_t)(V > 0 ? V : 1)) + align_up(sizeof(int32_t) * 3 * (size_t)(T > 0 ? T : 1));
+    const PairPlan& p = r->plan;
+    ReqLayout L;
+    size_t o = 0;
+    L.rec = o;
+    o += align_up(wd_tri_record_bytes(sv->cfg.precision) * (size_t)(T > 0 ? T : 1));
+    L.partial = o;
+    if (p.nchunks > 1) o += align_up(sizeof(double) * 2 * (size_t)p.nchunks * (size_t)p.n_nodes);
+    L.ppartial = o;
+    if (r->precise) o += align_up(wd_precise_partial_bytes(r->pplan, r->precise->n));
+    L.blockD = o;
+    o += align_up(sizeof(double) * (size_t)(p.n_nb > 0 ? p.n_nb : 1));
+    L.cnt = o;
+    L.done = L.cnt + sizeof(int) * (size_t)(p.n_nb > 0 ? p.n_nb : 1);
+    o += align_up(L.done + sizeof(int) - L.cnt);
+    L.verts = o;
+    o += align_up(sizeof(double) * 3 * (size_t)(V > 0 ? V : 1));
+    L.tris = o;
+    o += align_up(sizeof(int32_t) * 3 * (size_t)(T > 0 ? T : 1));
+    L.end = o;
+    return L;
 }
 
 void finish(wd_server* sv, Request* r, wd_status status, double result)
@@ -199,49 +238,62 @@ void release_slot(wd_server* sv, Request* r)
     }
 }
 
-wd_status capture_graph(wd_server* sv)
+ServeTable* table_head(wd_server* sv, int b) { return reinterpret_cast<ServeTable*>(sv->h_table[b]); }
+ServeRange* table_ranges(wd_server* sv, int b) { return reinterpret_cast<ServeRange*>(sv->h_table[b] + sv->off_ranges); }
+ServeReq* table_reqs(wd_server* sv, int b) { return reinterpret_cast<ServeReq*>(sv->h_table[b] + sv->off_reqs); }
+
+// One graph per table buffer: table in, batched kernels, result slots out.
+// (The worker brackets each replay with events recorded on the stream.)
+wd_status capture_graph(wd_server* sv, int b)
 {
     cudaStream_t s = sv->stream;
-    const ServeTable* d_head = reinterpret_cast<const ServeTable*>(sv->d_table);
-    const ServeReq* d_reqs = reinterpret_cast<const ServeReq*>(sv->d_table + sv->off_reqs);
-    const ServeItem* d_items = reinterpret_cast<const ServeItem*>(sv->d_table + sv->off_items);
-    const ServeFin* d_fin = reinterpret_cast<const ServeFin*>(sv->d_table + sv->off_fin);
+    ServeTable* d_head = reinterpret_cast<ServeTable*>(sv->d_table[b]);
+    const ServeRange* d_ranges = reinterpret_cast<const ServeRange*>(sv->d_table[b] + sv->off_ranges);
+    const ServeReq* d_reqs = reinterpret_cast<const ServeReq*>(sv->d_table[b] + sv->off_reqs);
     WD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemcpyAsync(sv->d_table, sv->h_table, sv->table_bytes, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(sv->d_table[b], sv->h_table[b], sv->table_bytes, cudaMemcpyHostToDevice, s);
+    const int64_t before = sv->ctx->launches;
     wd_status st = WD_OK;
-    if (e == cudaSuccess)
-        st = wd_launch_serve(sv->ctx, sv->cfg.precision, sv->grid, d_head, d_reqs, d_items, d_fin, sv->d_results, s);
+    if (e == cudaSuccess) st = wd_launch_serve(sv->ctx, sv->cfg.precision, d_head, d_ranges, d_reqs, s);
+    sv->kernels_per_launch = (int)(sv->ctx->launches - before);
+    sv->ctx->launches = before;  // counted per replay instead
     if (e == cudaSuccess && st == WD_OK)
-        e = cudaMemcpyAsync(sv->h_results, sv->d_results, sizeof(double) * kMaxSlots, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(sv->h_results[b], sv->d_results, sizeof(double) * kMaxSlots, cudaMemcpyDeviceToHost, s);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
-    if (e != cudaSuccess) return wd_cuda_status(e, "serve graph capture");
-    if (st != WD_OK) return st;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return wd_cuda_status(e, "serve graph capture");
+    }
+    if (st != WD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
     if (e2 != cudaSuccess) return wd_cuda_status(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&sv->graph, g, 0);
+    e = cudaGraphInstantiate(&sv->graph[b], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return wd_cuda_status(e, "cudaGraphInstantiate");
     return WD_OK;
 }
 
-// Stage one admitted request: copy its mesh and build its triangle records.
+// Stage one admitted request: copy its mesh, build its triangle records, clear
+// its completion counters and make sure the weights for its s exist.
 wd_status stage_request(wd_server* sv, Request* r)
 {
     const int64_t T = (int64_t)r->tris.size() / 3;
     const int64_t V = (int64_t)r->verts.size() / 3;
+    const ReqLayout L = request_layout(sv, r);
     char* base = sv->d_arena + r->off;
-    const size_t o_rec = 0;
-    const size_t o_bd = o_rec + align_up(wd_tri_record_bytes(sv->cfg.precision) * (size_t)(T > 0 ? T : 1));
-    const size_t o_v = o_bd + align_up(sizeof(double) * (size_t)(r->n_nb > 0 ? r->n_nb : 1));
-    const size_t o_t = o_v + align_up(sizeof(double) * 3 * (size_t)(V > 0 ? V : 1));
     if (V > 0)
-        WD_CUDA(cudaMemcpyAsync(base + o_v, r->verts.data(), sizeof(double) * 3 * V, cudaMemcpyHostToDevice,
+        WD_CUDA(cudaMemcpyAsync(base + L.verts, r->verts.data(), sizeof(double) * 3 * V, cudaMemcpyHostToDevice,
                                 sv->stream));
     if (T > 0)
-        WD_CUDA(cudaMemcpyAsync(base + o_t, r->tris.data(), sizeof(int32_t) * 3 * T, cudaMemcpyHostToDevice,
+        WD_CUDA(cudaMemcpyAsync(base + L.tris, r->tris.data(), sizeof(int32_t) * 3 * T, cudaMemcpyHostToDevice,
                                 sv->stream));
-    wd_status st = wd_launch_stage(sv->ctx, sv->cfg.precision, reinterpret_cast<const double*>(base + o_v), V,
-                                   reinterpret_cast<const int32_t*>(base + o_t), T, 1.0, base + o_rec, 0, sv->stream);
+    WD_CUDA(cudaMemsetAsync(base + L.cnt, 0, L.done + sizeof(int) - L.cnt, sv->stream));
+    wd_status st = wd_launch_stage(sv->ctx, sv->cfg.precision, reinterpret_cast<const double*>(base + L.verts), V,
+                                   reinterpret_cast<const int32_t*>(base + L.tris), T, 1.0, base + L.rec, 0,
+                                   sv->stream);
     if (st != WD_OK) return st;
     RuleEntry& re = sv->rules[r->rule];
     if (!re.W.count(r->s)) {
@@ -249,18 +301,138 @@ wd_status stage_request(wd_server* sv, Request* r)
         if ((st = wd_rule_weights(sv->ctx, re.rule, r->s, &w, sv->stream)) != WD_OK) return st;
         re.W[r->s] = w;
     }
-    r->staged = true;
+    // the request's descriptor, the same in both tables
+    ServeReq q;
+    wd_pair_args_rule(re.rule, q.a);
+    q.a.tris = base + L.rec;
+    q.a.T = T;
+    q.a.W = re.W[r->s];
+    q.a.nu = re.nu;
+    q.a.partial = reinterpret_cast<double*>(base + L.partial);
+    q.a.blockD = reinterpret_cast<double*>(base + L.blockD);
+    q.a.cnt = reinterpret_cast<int*>(base + L.cnt);
+    q.a.done = reinterpret_cast<int*>(base + L.done);
+    q.a.out = sv->d_results + r->slot;
+    if (r->precise) {
+        q.a.precise_flag = r->precise->d_flag;
+        q.a.precise_list = r->precise->d_list;
+        q.a.n_precise = r->precise->n;
+        q.a.precise_partial = reinterpret_cast<double*>(base + L.ppartial);
+    }
+    q.p = r->plan;
+    q.pp = r->pplan;
+    for (int b = 0; b < kBuffers; ++b) table_reqs(sv, b)[r->slot] = q;
     return WD_OK;
+}
+
+int64_t item_pairs(const Request* r) { return (int64_t)r->plan.tiles_per_chunk * WD_TILE * WD_NPB; }
+
+// Fill table b for launch `seq`: round-robin shares of the pair budget over
+// the admitted queries, queries with the largest items first; one contiguous
+// range per query and kernel form (a per-node query's run of items may cross
+// from its plain items into its extended-precision ones). Lock held.
+int64_t build_launch(wd_server* sv, int b, int64_t seq, double* pairs_out)
+{
+    ServeTable* head = table_head(sv, b);
+    ServeRange* ranges = table_ranges(sv, b);
+    std::vector<Request*> act;
+    for (Request* r : sv->slots)
+        if (r && !r->cancel && r->next_item < r->n_items) act.push_back(r);
+    std::stable_sort(act.begin(), act.end(), [](const Request* x, const Request* y) {
+        return item_pairs(x) > item_pairs(y);
+    });
+    std::vector<int64_t> take(act.size(), 0);
+    double pairs = 0.0;
+    bool progress = true;
+    while (progress && pairs < (double)sv->cfg.pairs_per_launch) {
+        progress = false;
+        for (size_t i = 0; i < act.size() && pairs < (double)sv->cfg.pairs_per_launch; ++i) {
+            const int64_t left = act[i]->n_items - act[i]->next_item - take[i];
+            if (left <= 0) continue;
+            const int64_t k = left < kRoundItems ? left : kRoundItems;
+            take[i] += k;
+            pairs += (double)k * (double)item_pairs(act[i]);
+            progress = true;
+        }
+    }
+    int n_rg[SERVE_FORMS] = {0, 0, 0};
+    int64_t n_it[SERVE_FORMS] = {0, 0, 0};
+    auto add_range = [&](int f, int slot, int64_t first, int64_t count) {
+        ServeRange& g = ranges[f * WD_SERVE_RANGES + n_rg[f]++];
+        g.req = slot;
+        g.count = (int)count;
+        g.first = first;
+        g.start = n_it[f];
+        n_it[f] += count;
+    };
+    for (size_t i = 0; i < act.size(); ++i) {
+        if (take[i] == 0) continue;
+        Request* r = act[i];
+        const int64_t a = r->next_item, e = r->next_item + take[i];
+        if (r->plan.radial) {
+            add_range(SERVE_RADIAL, r->slot, a, e - a);
+        } else {
+            const int64_t m = r->plan.n_items;  // plain items [0, m), then the precise ones
+            if (a < m) add_range(SERVE_NODE, r->slot, a, std::min(e, m) - a);
+            if (e > m) add_range(SERVE_PRECISE, r->slot, std::max(a, m) - m, e - std::max(a, m));
+        }
+        r->next_item = e;
+        r->last_seq = seq;
+        if (r->next_item == r->n_items) r->finish_seq = seq;
+    }
+    for (int f = 0; f < SERVE_FORMS; ++f) {
+        head->n_ranges[f] = n_rg[f];
+        head->n_items[f] = n_it[f];
+        head->next[f] = 0;
+    }
+    *pairs_out = pairs;
+    return n_it[0] + n_it[1] + n_it[2];
+}
+
+// Retire launch `seq` (complete on the device): deliver the queries it
+// finished and free cancelled queries with no work left in flight. Lock held.
+void retire_launch(wd_server* sv, int64_t seq)
+{
+    const int b = (int)(seq % kBuffers);
+    bool any = false;
+    for (Request* r : sv->slots) {
+        if (!r) continue;
+        if (r->finish_seq == seq) {
+            const double d = sv->h_results[b][r->slot];
+            sv->st.pairs += (double)r->plan.n_tris * (double)r->plan.n_nodes;
+            release_slot(sv, r);
+            finish(sv, r, r->cancel ? WD_ECANCELLED : WD_OK, d);
+            any = true;
+        } else if (r->cancel && r->last_seq <= seq) {
+            release_slot(sv, r);
+            finish(sv, r, WD_ECANCELLED, 0.0);
+            any = true;
+        }
+    }
+    if (any) sv->cv_done.notify_all();
+}
+
+// after a CUDA error of the worker (its text is this thread's last error)
+void fail_all(wd_server* sv, wd_status status)
+{
+    sv->fatal = status;
+    sv->fatal_msg = wd_last_error(nullptr);
+    for (Request*& r : sv->slots)
+        if (r) {
+            Request* q = r;
+            q->why = sv->fatal_msg;
+            release_slot(sv, q);
+            finish(sv, q, status, 0.0);
+        }
+    sv->cv_done.notify_all();
 }
 
 void worker_main(wd_server* sv)
 {
     cudaSetDevice(sv->ctx->device);
-    ServeTable* head = reinterpret_cast<ServeTable*>(sv->h_table);
-    ServeReq* reqs = reinterpret_cast<ServeReq*>(sv->h_table + sv->off_reqs);
-    ServeItem* items = reinterpret_cast<ServeItem*>(sv->h_table + sv->off_items);
-    ServeFin* fin = reinterpret_cast<ServeFin*>(sv->h_table + sv->off_fin);
     std::vector<Request*> to_stage;
+    int64_t seq = 0;        // launches issued
+    int64_t retired = 0;    // launches retired (all below are complete)
     for (;;) {
         to_stage.clear();
         {
@@ -286,6 +458,13 @@ void worker_main(wd_server* sv)
                         ++it;
                     }
                 }
+                // cancelled admitted requests with nothing in flight
+                for (Request* r : sv->slots)
+                    if (r && r->cancel && r->last_seq < retired) {
+                        release_slot(sv, r);
+                        finish(sv, r, WD_ECANCELLED, 0.0);
+                        sv->cv_done.notify_all();
+                    }
                 // admit in arrival order while a slot and arena space are free
                 while (!sv->pending.empty()) {
                     Request* r = sv->pending.front();
@@ -296,7 +475,7 @@ void worker_main(wd_server* sv)
                             break;
                         }
                     if (slot < 0) break;
-                    const size_t need = request_bytes(sv, r);
+                    const size_t need = request_layout(sv, r).end;
                     size_t off = 0;
                     if (!sv->arena.alloc(need, &off)) break;
                     r->off = off;
@@ -308,111 +487,67 @@ void worker_main(wd_server* sv)
                     sv->st.admitted++;
                     to_stage.push_back(r);
                 }
-                bool active = false;
-                for (Request* r : sv->slots) active = active || r != nullptr;
-                if (active || !to_stage.empty()) break;
+                bool work = !to_stage.empty() || seq > retired;
+                for (Request* r : sv->slots) work = work || r != nullptr;
+                if (work) break;
                 if (sv->stopping) return;
                 sv->cv_work.wait_for(lk, std::chrono::milliseconds(sv->cfg.timeout_ms > 0 ? 1 : 20));
             }
         }
-        // stage newly admitted requests (outside the lock)
+        // stage newly admitted requests (outside the lock; stream-ordered
+        // before the next launch)
         for (Request* r : to_stage) {
             wd_status st = stage_request(sv, r);
             if (st != WD_OK) {
                 std::lock_guard<std::mutex> lk(sv->mu);
+                r->why = wd_last_error(nullptr);
                 release_slot(sv, r);
                 finish(sv, r, st, 0.0);
                 sv->cv_done.notify_all();
             }
         }
-        // build the launch: round-robin node blocks of every admitted request
-        std::vector<Request*> finishing;
-        int n_items = 0;
+        // build and enqueue launch `seq` into the buffer of launch seq - 2,
+        // which is retired (at most kBuffers launches are in flight)
+        int64_t n_items = 0;
         double pairs = 0.0;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            for (int i = 0; i < sv->cfg.max_slots; ++i) {
-                Request* r = sv->slots[i];
-                if (r && r->cancel) {
-                    release_slot(sv, r);
-                    finish(sv, r, WD_ECANCELLED, 0.0);
-                    sv->cv_done.notify_all();
-                    r = nullptr;
-                }
-                if (!r) continue;
-                RuleEntry& re = sv->rules[r->rule];
-                char* base = sv->d_arena + r->off;
-                const int64_t T = (int64_t)r->tris.size() / 3;
-                ServeReq q;
-                q.rec = base;
-                q.T = T;
-                q.xi = re.rule->d_xi;
-                q.n = re.rule->n_eval;
-                const bool radial = sv->cfg.precision == WD_MIXED && re.rule->d_rad;
-                q.rad = radial ? re.rule->d_rad : nullptr;
-                q.dir = radial ? re.rule->d_dir : nullptr;
-                q.n_rad = re.rule->n_rad;
-                q.n_rg = (re.rule->n_rad + WD_RAD_NR - 1) / WD_RAD_NR;
-                q.n_dir = re.rule->n_dir;
-                q.W = re.W[r->s];
-                q.nu = re.nu;
-                q.blockD = reinterpret_cast<double*>(
-                    base + align_up(wd_tri_record_bytes(sv->cfg.precision) * (size_t)(T > 0 ? T : 1)));
-                reqs[i] = q;
-            }
-            bool progress = true;
-            while (progress && n_items < kMaxItems && pairs < (double)sv->cfg.pairs_per_launch) {
-                progress = false;
-                for (int i = 0; i < sv->cfg.max_slots && n_items < kMaxItems; ++i) {
-                    Request* r = sv->slots[i];
-                    if (!r || r->next_nb >= r->n_nb) continue;
-                    const int64_t T = reqs[i].T;
-                    for (int b = 0; b < kRoundRobinBlocks && r->next_nb < r->n_nb && n_items < kMaxItems; ++b) {
-                        items[n_items].req = i;
-                        items[n_items].nb = r->next_nb++;
-                        n_items++;
-                        pairs += (double)T * WD_NPB;
-                    }
-                    if (r->next_nb >= r->n_nb) finishing.push_back(r);
-                    progress = true;
-                }
-            }
-            head->n_items = n_items;
-            head->n_fin = (int)finishing.size();
-            for (size_t f = 0; f < finishing.size(); ++f) {
-                fin[f].req = finishing[f]->slot;
-                fin[f].n_nb = finishing[f]->n_nb;
-                fin[f].out = finishing[f]->slot;
-            }
+            if (seq - retired < kBuffers) n_items = build_launch(sv, (int)(seq % kBuffers), seq, &pairs);
         }
-        if (n_items == 0 && finishing.empty()) continue;
-        const auto t0 = Clock::now();
-        WdRange nvtx_range("wd_serve launch");
-        cudaError_t e = cudaGraphLaunch(sv->graph, sv->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
-        const auto t1 = Clock::now();
-        std::lock_guard<std::mutex> lk(sv->mu);
-        sv->busy_s += std::chrono::duration<double>(t1 - t0).count();
-        sv->st.launches++;
-        sv->st.pairs += pairs;
-        if (e != cudaSuccess) {
-            wd_cuda_status(e, "serve launch");
-            sv->fatal = WD_ECUDA;
-            for (Request*& r : sv->slots)
-                if (r) {
-                    Request* q = r;
-                    release_slot(sv, q);
-                    finish(sv, q, WD_ECUDA, 0.0);
-                }
-            sv->cv_done.notify_all();
-            return;
+        if (n_items > 0) {
+            WdRange nvtx_range("wd_serve launch");
+            const int b = (int)(seq % kBuffers);
+            cudaError_t e = cudaEventRecord(sv->ev_start[b], sv->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(sv->graph[b], sv->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(sv->ev_end[b], sv->stream);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (e != cudaSuccess) {
+                fail_all(sv, wd_cuda_status(e, "serve launch"));
+                return;
+            }
+            sv->ctx->launches += sv->kernels_per_launch;
+            sv->st.launches++;
+            ++seq;
         }
-        for (Request* r : finishing) {
-            const double d = sv->h_results[r->slot];
-            release_slot(sv, r);
-            finish(sv, r, r->cancel ? WD_ECANCELLED : WD_OK, d);
+        // retire the oldest launch once the next one is queued behind it (or
+        // when nothing else can be queued)
+        if (seq > retired && (seq - retired >= kBuffers || n_items == 0)) {
+            const int b = (int)(retired % kBuffers);
+            const cudaError_t e = cudaEventSynchronize(sv->ev_end[b]);
+            float ms = 0.0f;
+            if (e == cudaSuccess && cudaEventElapsedTime(&ms, sv->ev_start[b], sv->ev_end[b]) != cudaSuccess) {
+                cudaGetLastError();  // no timing for this launch; the work itself completed
+                ms = 0.0f;
+            }
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (e != cudaSuccess) {
+                fail_all(sv, wd_cuda_status(e, "serve launch"));
+                return;
+            }
+            sv->busy_s += 1e-3 * ms;
+            retire_launch(sv, retired);
+            ++retired;
         }
-        if (!finishing.empty()) sv->cv_done.notify_all();
     }
 }
 
@@ -433,14 +568,21 @@ extern "C" wd_status wd_serve_start(wd_ctx* ctx, const wd_serve_config* cfg, wd_
     sv->ctx = ctx;
     sv->cfg = *cfg;
     sv->slots.assign(cfg->max_slots, nullptr);
+    auto release_all = [](wd_server* v) {
+        for (int b = 0; b < kBuffers; ++b) {
+            if (v->graph[b]) cudaGraphExecDestroy(v->graph[b]);
+            if (v->ev_start[b]) cudaEventDestroy(v->ev_start[b]);
+            if (v->ev_end[b]) cudaEventDestroy(v->ev_end[b]);
+            cudaFree(v->d_table[b]);
+            cudaFreeHost(v->h_table[b]);
+            cudaFreeHost(v->h_results[b]);
+        }
+        if (v->stream) cudaStreamDestroy(v->stream);
+        cudaFree(v->d_arena);
+        cudaFree(v->d_results);
+    };
     auto fail = [&](wd_status s) {
-        if (sv->graph) cudaGraphExecDestroy(sv->graph);
-        if (sv->stream) cudaStreamDestroy(sv->stream);
-        cudaFree(sv->d_arena);
-        cudaFree(sv->d_table);
-        cudaFree(sv->d_results);
-        cudaFreeHost(sv->h_table);
-        cudaFreeHost(sv->h_results);
+        release_all(sv);
         delete sv;
         return s;
     };
@@ -461,24 +603,31 @@ extern "C" wd_status wd_serve_start(wd_ctx* ctx, const wd_serve_config* cfg, wd_
         return fail(WD_ENOMEM);
     }
     sv->arena.init(sv->d_arena, (size_t)cfg->mem_cap_bytes);
-    sv->off_reqs = align_up(sizeof(ServeTable));
-    sv->off_items = sv->off_reqs + align_up(sizeof(ServeReq) * kMaxSlots);
-    sv->off_fin = sv->off_items + align_up(sizeof(ServeItem) * kMaxItems);
-    sv->table_bytes = sv->off_fin + align_up(sizeof(ServeFin) * kMaxSlots);
-    if (cudaHostAlloc(&sv->h_table, sv->table_bytes, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc(&sv->h_results, sizeof(double) * kMaxSlots, cudaHostAllocDefault) != cudaSuccess ||
-        wd_dev_alloc(&sv->d_table, sv->table_bytes, "serving table") != cudaSuccess ||
-        wd_dev_alloc(&sv->d_results, sizeof(double) * kMaxSlots, "serving results") != cudaSuccess) {
+    sv->off_ranges = align_up(sizeof(ServeTable));
+    sv->off_reqs = sv->off_ranges + align_up(sizeof(ServeRange) * SERVE_FORMS * WD_SERVE_RANGES);
+    sv->table_bytes = sv->off_reqs + align_up(sizeof(ServeReq) * kMaxSlots);
+    bool ok = wd_dev_alloc(&sv->d_results, sizeof(double) * kMaxSlots, "serving results") == cudaSuccess;
+    for (int b = 0; ok && b < kBuffers; ++b)
+        ok = cudaHostAlloc(&sv->h_table[b], sv->table_bytes, cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc(&sv->h_results[b], sizeof(double) * kMaxSlots, cudaHostAllocDefault) == cudaSuccess &&
+             wd_dev_alloc(&sv->d_table[b], sv->table_bytes, "serving table") == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         wd_set_error("cannot allocate the serving tables");
         return fail(WD_ENOMEM);
     }
-    std::memset(sv->h_table, 0, sv->table_bytes);
-    sv->grid = wd_serve_resident(ctx, cfg->precision);
-    if ((st = capture_graph(sv)) != WD_OK) return fail(st);
+    for (int b = 0; b < kBuffers; ++b) {
+        std::memset(sv->h_table[b], 0, sv->table_bytes);
+        if (cudaEventCreate(&sv->ev_start[b]) != cudaSuccess || cudaEventCreate(&sv->ev_end[b]) != cudaSuccess)
+            return fail(wd_cuda_status(cudaGetLastError(), "cudaEventCreate"));
+    }
+    // occupancy queries before the capture (they are cached per context)
+    for (int f = 0; f < SERVE_FORMS; ++f) wd_serve_resident(ctx, cfg->precision, f);
+    for (int b = 0; b < kBuffers; ++b)
+        if ((st = capture_graph(sv, b)) != WD_OK) return fail(st);
     sv->drop_nth = wd_fault_drop_completion();
-    wd_log(3, "server started: %d slots, arena %lld bytes, %d rules, grid %d", cfg->max_slots,
-           (long long)cfg->mem_cap_bytes, cfg->n_rules, sv->grid);
+    wd_log(3, "server started: %d slots, arena %lld bytes, %d rules, %d kernels per launch", cfg->max_slots,
+           (long long)cfg->mem_cap_bytes, cfg->n_rules, sv->kernels_per_launch);
     sv->worker = std::thread(worker_main, sv);
     *out = sv;
     return WD_OK;
@@ -504,17 +653,25 @@ extern "C" wd_status wd_serve_submit(wd_server* sv, const wd_mesh* m, double s, 
     r->s = s;
     r->rule = rule;
     {
-        // node blocks: radius x direction blocks for ball rules in the mixed path
-        const wd_rule* ru = sv->rules[rule].rule;
-        if (sv->cfg.precision == WD_MIXED && ru->d_rad)
-            r->n_nb = (int)(((ru->n_dir + WD_RAD_ND - 1) / WD_RAD_ND) * ((ru->n_rad + WD_RAD_NR - 1) / WD_RAD_NR));
-        else
-            r->n_nb = (int)((ru->n_eval + WD_NPB - 1) / WD_NPB);
+        // the plan of this query's own wd_distance launch, items capped in size
+        wd_rule* ru = sv->rules[rule].rule;
+        wd_status pst = wd_plan_pair_serve(sv->ctx, ru, sv->cfg.precision, m->n_tris, kMaxItemTiles, &r->plan);
+        if (pst == WD_OK && sv->cfg.precision == WD_MIXED && !r->plan.radial) {
+            // the extended-precision blocks of wd_distance's per-node plan
+            pst = wd_rule_precise(sv->ctx, ru, s, &r->precise);
+            if (pst == WD_OK && r->precise->n == 0) r->precise = nullptr;
+            if (pst == WD_OK && r->precise) r->pplan = wd_precise_plan(sv->ctx, r->plan, r->precise->n, MODE_DIST);
+        }
+        if (pst != WD_OK) {
+            delete r;
+            return pst;
+        }
+        r->n_items = r->plan.n_items + (r->precise ? r->pplan.n_items : 0);
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->fatal != WD_OK) {
         delete r;
-        wd_set_error("the serving loop stopped after a CUDA error");
+        wd_set_error("the serving loop stopped after a CUDA error: " + sv->fatal_msg);
         return sv->fatal;
     }
     if ((int)sv->pending.size() >= sv->cfg.max_pending) {
@@ -523,7 +680,7 @@ extern "C" wd_status wd_serve_submit(wd_server* sv, const wd_mesh* m, double s, 
         wd_set_error("serving queue full");
         return WD_EBUSY;
     }
-    if (request_bytes(sv, r) > (size_t)sv->cfg.mem_cap_bytes) {
+    if (request_layout(sv, r).end > (size_t)sv->cfg.mem_cap_bytes) {
         sv->st.rejected++;
         delete r;
         wd_set_error("query larger than the serving memory cap");
@@ -572,7 +729,7 @@ extern "C" wd_status wd_serve_wait(wd_server* sv, uint64_t ticket, int timeout_m
         }
     }
     if (r->state == FAILED) {
-        wd_set_error("query failed");
+        wd_set_error("query failed: " + r->why);
         return r->status;
     }
     if (dist2) *dist2 = r->result;
@@ -631,15 +788,20 @@ extern "C" wd_status wd_serve_stop(wd_server* sv)
     if (sv->worker.joinable()) sv->worker.join();
     cudaSetDevice(sv->ctx->device);
     cudaStreamSynchronize(sv->stream);
-    if (sv->graph) cudaGraphExecDestroy(sv->graph);
+    for (int b = 0; b < kBuffers; ++b) {
+        if (sv->graph[b]) cudaGraphExecDestroy(sv->graph[b]);
+        if (sv->ev_start[b]) cudaEventDestroy(sv->ev_start[b]);
+        if (sv->ev_end[b]) cudaEventDestroy(sv->ev_end[b]);
+        cudaFree(sv->d_table[b]);
+        cudaFreeHost(sv->h_table[b]);
+        cudaFreeHost(sv->h_results[b]);
+    }
     cudaStreamDestroy(sv->stream);
     cudaFree(sv->d_arena);
-    cudaFree(sv->d_table);
     cudaFree(sv->d_results);
-    cudaFreeHost(sv->h_table);
-    cudaFreeHost(sv->h_results);
     for (auto& kv : sv->all) delete kv.second;
     const wd_status fatal = sv->fatal;
+    if (fatal != WD_OK) wd_set_error("the serving loop had stopped after a CUDA error: " + sv->fatal_msg);
     delete sv;
     return fatal;
 }

@@ -236,7 +236,7 @@ ADJOINT_NS = (16, 32)
 ADJOINT_SIGMA = 0.01
 ADJOINT_SEEDS = tuple(range(64))
 
-# the paper's own experiment (Sec. 4.2, Fig. 4b): icosahedral T_N, N = 0..7,
+# the paper's own experiment (Sec. 4.2, Fig. 3b): icosahedral T_N, N = 0..7,
 # against the unit sphere in H_{-10} on the cube trapezoid rule xi_max = 5,
 # M = 128 (paper's 2 pi convention); this library's order s = 10
 PAPER_XI_MAX = 5.0

@@ -1,7 +1,7 @@
 """The paper's own experiment on the GPU: the cube trapezoid rule in the
 paper's 2 pi convention (Sec. 3.2), the unit sphere's H_{-s} norm against its
 closed form, icosahedral T_N against the oracle, and the O(4^-N) convergence
-of Fig. 4b reaching about 1e-5 at N = 7 (Sec. 4.2)."""
+of Fig. 3b reaching about 1e-5 at N = 7 (Sec. 4.2)."""
 import math
 
 import numpy as np
@@ -57,7 +57,7 @@ def test_cube_rule_rejects_bad_descriptors(ctx):
 @pytest.mark.parametrize("prec", [wd.WD_FP64, wd.WD_MIXED])
 def test_sphere_norm_on_the_paper_rule(ctx, prec):
     # no triangles: D = sum W |sigma^|^2, the rule's value of the sphere's
-    # squared norm, converged to round-off for s = -10 at M = 128 (Fig. 3b)
+    # squared norm, converged to round-off for s = -10 at M = 128 (Fig. 1b)
     rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
     d = ctx.distance(rule, EMPTY_V, EMPTY_T, None, synth.PAPER_S, prec)
     assert d == pytest.approx(sphere_norm2(synth.PAPER_S), rel=1e-12)
@@ -106,10 +106,27 @@ def test_paper_fig4b_convergence(ctx):
     assert 3e-6 < err[7] < 3e-5, err
 
 
-def test_paper_rule_mixed_matches_fp64_at_N5(ctx):
-    # the mixed path on the paper's rule where D / |mu|^2 is ~1e-9
+@pytest.mark.parametrize("N", [5, 6])
+def test_paper_rule_mixed_matches_fp64(ctx, N):
+    # the mixed path on the paper's rule where D / |mu|^2 is 1e-9 (N = 5) and
+    # 6e-11 (N = 6): D rests on the few thousand nodes with |eta| < 1, which
+    # the extended-precision blocks take; bar 1e-6 as everywhere
     rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
-    v, t = synth.icosphere_recursive(5)
+    v, t = synth.icosphere_recursive(N)
     d64 = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_FP64)
     dmx = ctx.distance(rule, v, t, None, synth.PAPER_S, wd.WD_MIXED)
-    assert dmx == pytest.approx(d64, rel=1e-6)
+    assert dmx == pytest.approx(d64, rel=1e-6), (dmx - d64) / d64
+
+
+def test_extended_precision_blocks_follow_the_weight(ctx):
+    """T_4 on the paper's rule at M = 32: the mixed D is the oracle's within
+    1e-7 both for s = 10, where a few node blocks near the origin take the
+    extended-precision form, and for s = 0.01, where every weight is within
+    1e-3 of the largest and every block takes it."""
+    v, t = synth.icosphere_recursive(4)
+    xo, wo = oracle.cube_rule(synth.PAPER_XI_MAX, 32, True)
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, 32, True)
+    for s in (synth.PAPER_S, 0.01):
+        d_or = oracle.distance(xo, wo, s, v, t, wscale=oracle.PAPER_WSCALE)
+        dmx = ctx.distance(rule, v, t, None, s, wd.WD_MIXED)
+        assert dmx == pytest.approx(d_or, rel=1e-7), (s, (dmx - d_or) / d_or)

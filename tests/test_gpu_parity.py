@@ -233,3 +233,37 @@ def test_mixed_matches_fp64_on_the_refinement_sweep(ctx, n, shells, s):
     d64 = ctx.distance(rule, v, t, None, s, FP64)
     dmx = ctx.distance(rule, v, t, None, s, MIXED)
     assert abs(dmx - d64) < 1e-6 * d64, (dmx, d64, (dmx - d64) / d64)
+
+
+def test_radial_shell_windows(ctx):
+    """A ball rule split into radial-shell windows: the windows' nodes and
+    weights are the full rule's, in order; D over a partition of the shells
+    adds up to D over the full rule (both precisions); and a 32-aligned
+    window's mixed transform is the full rule's, bit for bit."""
+    desc = (24.0, 96, 8, 12, True)
+    full = ctx.rule(*desc)
+    xi, w = wd.wd_rule_copy_nodes(full)
+    per = len(xi) // desc[1]
+    v, t = synth.icosphere(6)
+    v = synth.jitter_isotropic(v, 0.01, 3)
+    # float64: any partition; mixed: 32-aligned windows (the same float32
+    # operations per node as the full rule, so only the final sums differ)
+    for prec, bounds in ((FP64, [(0, 7), (7, 40), (40, 96)]), (MIXED, [(0, 32), (32, 64), (64, 96)])):
+        parts = []
+        for a, b in bounds:
+            win = ctx.rule_shells(*desc, a, b)
+            xw, ww = wd.wd_rule_copy_nodes(win)
+            assert np.array_equal(xw, xi[a * per:b * per]) and np.array_equal(ww, w[a * per:b * per])
+            assert wd.wd_rule_info(win) == ((b - a) * per, (b - a) * desc[2] * desc[3])
+            parts.append(ctx.distance(win, v, t, None, 1.0, prec))
+        d_full = ctx.distance(full, v, t, None, 1.0, prec)
+        assert abs(sum(parts) - d_full) < 1e-13 * d_full, (prec, sum(parts), d_full)
+    win = ctx.rule_shells(*desc, 32, 64)
+    assert np.array_equal(ctx.mesh_ft(win, v, t, MIXED), ctx.mesh_ft(full, v, t, MIXED)[32 * per:64 * per])
+    assert ctx.rule_shells(*desc, 32, 64).value == win.value  # cached by descriptor and window
+    for a, b in ((-1, 4), (4, 4), (90, 97)):
+        with pytest.raises(wd.WDError) as e:
+            ctx.rule_shells(*desc, a, b)
+        assert e.value.status == wd.WD_EINVAL
+    with pytest.raises(wd.WDError):
+        wd.wd_build_freq_rule_shells(ctx.handle, 5.0, 16, 0, 0, True, 0, 4)  # no windows of n_polar = 0

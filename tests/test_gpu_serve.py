@@ -1,10 +1,12 @@
 """Serving loop: continuous batching gives every query the same result alone
-and in the mix; admission, queue limits, bounded waits and cancellation."""
+and in the mix, and the same as wd_distance and the oracle; admission, queue
+limits, bounded waits and cancellation."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -52,12 +54,37 @@ def test_results_alone_and_in_the_mix(ctx, prec):
         st = wd.wd_serve_stats(sv)
     finally:
         wd.wd_serve_stop(sv)
-    tol = 1e-12 if prec == wd.WD_FP64 else 1e-6
-    for a, b in zip(alone, mixed):
-        assert abs(a - b) <= tol * a, (a, b)
-    for a, b in zip(alone[:4], one_by_one):
-        assert abs(a - b) <= tol * a
+    # every query runs the items of its own wd_distance plan, summed in the
+    # plan's fixed order: the same bits alone, in the mix and from wd_distance
+    assert mixed == alone and one_by_one == alone[:4]
     assert st["completed"] == 28 and st["launches"] >= 2 and st["failed"] == 0
+
+
+@pytest.mark.parametrize("prec", [wd.WD_MIXED, wd.WD_FP64])
+def test_served_results_match_the_oracle(ctx, prec):
+    """Served D against the CPU oracle on the serving rules' shapes (R = 64:
+    64 x 32 x 64 and R = 128: 128 x 48 x 96, Hermitian), small meshes mixed
+    with a large one so that the small queries share launches with it."""
+    rules = [(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian) for R in synth.SERVE_RULES.values()]
+    small = []
+    for i, (n, R) in enumerate(((2, 64.0), (3, 128.0), (5, 64.0))):
+        v, t = synth.icosphere(n)
+        v = synth.jitter_isotropic(v @ synth.haar_rotation(40 + i).T, 1e-3 * synth.mean_edge_length(v, t), 40 + i)
+        small.append((v, t, 1.0 + (i % 2), R))
+    big_v, big_t = synth.icosphere(40)
+    sv = wd.wd_serve_start(ctx.handle, rules, precision=prec, max_slots=8, pairs_per_launch=2_000_000_000)
+    try:
+        tk_big = wd.wd_serve_submit(sv, big_v, big_t, 1.0, 128.0)
+        tks = [wd.wd_serve_submit(sv, v, t, s, R) for (v, t, s, R) in small]
+        served = [wd.wd_serve_wait(sv, tk, 600000) for tk in tks]
+        wd.wd_serve_wait(sv, tk_big, 600000)
+    finally:
+        wd.wd_serve_stop(sv)
+    tol = 1e-12 if prec == wd.WD_FP64 else 1e-6
+    for (v, t, s, R), got in zip(small, served):
+        xo, wo = oracle.ball_rule(*next(r for r in rules if r[0] == R))
+        want = oracle.distance(xo, wo, s, v, t)
+        assert abs(got - want) <= tol * want, (R, len(t), got, want, (got - want) / want)
 
 
 def test_admission_limits_waits_and_cancel(ctx):
@@ -143,9 +170,4 @@ def test_lattice_rule_queries(ctx, prec):
         served = [wd.wd_serve_wait(sv, tk, 60000) for tk in tickets]
     finally:
         wd.wd_serve_stop(sv)
-    # float64: wd_distance splits these small rules' triangles into chunks, the
-    # server sums them in one pass; that order difference (1e-16 of mu^) reaches
-    # D amplified by |mu^| / |mu^ - nu^|, about 30 here
-    tol = 1e-10 if prec == wd.WD_FP64 else 1e-6
-    for a, b in zip(alone, served):
-        assert abs(a - b) <= tol * a, (a, b)
+    assert served == alone

@@ -321,7 +321,7 @@ def test_cube_rule_is_the_product_trapezoid(herm):
 
 
 def test_cube_rule_sphere_norm_as_the_paper_reports():
-    # Sec. 4.1 (Fig. 3b): with xmax = 5 the cube trapezoidal rule for the
+    # Sec. 4.1 (Fig. 1b): with xmax = 5 the cube trapezoidal rule for the
     # unit sphere's H_s norm, against the closed form Eq.
     # (sphere_sobolev_exact), is limited by truncation at about 1e-7 for
     # s = -5, while for s = -10 it keeps converging to round-off; the paper's
