@@ -41,6 +41,9 @@ UNIT = "Gpair/s"
 # arithmetic. The pipe bound per SM per clock is max(N_FP32/128, N_MUFU/16).
 N_FP32_PER_PAIR = 60
 N_MUFU_PER_PAIR = 6
+# Algorithmic work of one (triangle, node) pair of the mixed radial adjoint
+# (Taylor branch): FP32 pipe operations
+N_FP32_PER_PAIR_ADJOINT = 80
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
 # DRAM bytes (read + write) of one launch of the radial pair kernel on the
 # large query, from an ncu capture of the current kernel; None when the kernel
@@ -395,8 +398,13 @@ def adjoint_bench(wd, ctx):
     R = synth.ADJOINT_RULE
     rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
     n_eval, _ = wd.wd_rule_info(rule)
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = measured_peaks()[0].get("sm_max_mhz", 2032.0)
     res = {"rule": "R=%g %dx%dx%d herm (%d nodes evaluated)" % (R.R, R.n_r, R.n_polar, R.n_azim, n_eval),
-           "precision": "mixed", "s": 1.0, "sigma": synth.ADJOINT_SIGMA, "meshes": len(synth.ADJOINT_SEEDS)}
+           "precision": "mixed", "s": 1.0, "sigma": synth.ADJOINT_SIGMA, "meshes": len(synth.ADJOINT_SEEDS),
+           "adjoint_roofline_basis": "%d SMs x %.0f MHz / (%d FP32 ops/128) clk per pair: the Taylor branch of the "
+                                     "radial adjoint (phase, exponential, residual rotation, the tail and its two "
+                                     "partials in r^2, six accumulations)" % (sm_count, mhz, N_FP32_PER_PAIR_ADJOINT)}
     for n in synth.ADJOINT_NS:
         dev = []
         for sd in synth.ADJOINT_SEEDS:
@@ -415,6 +423,15 @@ def adjoint_bench(wd, ctx):
         e1.record()
         torch.cuda.synchronize()
         sec = e0.elapsed_time(e1) / 1e3
+        # the forward pass alone on the same meshes: the gradient's time minus
+        # this is the adjoint's (its kernels and the vertex scatter)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record()
+        for i, (v, t) in enumerate(dev):
+            wd.wd_distance_dev(ctx.handle, rule, v, t, None, 1.0, wd.WD_MIXED, out[i:i + 1])
+        e3.record()
+        torch.cuda.synchronize()
+        fwd = e2.elapsed_time(e3) / 1e3
         T = dev[0][1].shape[0]
         g64 = torch.zeros_like(dev[0][0])
         o64 = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -427,6 +444,10 @@ def adjoint_bench(wd, ctx):
             "n_tris": T, "seconds": sec, "mesh_grads_per_s": len(dev) / sec,
             "gpairs_per_s": len(dev) * T * n_eval / sec / 1e9,
             "pair_note": "T x nodes per mesh counted once; each is evaluated in the forward and in the adjoint",
+            "forward_seconds": fwd, "adjoint_seconds": sec - fwd,
+            "adjoint_gpairs_per_s": len(dev) * T * n_eval / (sec - fwd) / 1e9,
+            "adjoint_roofline_frac": len(dev) * T * n_eval / (sec - fwd)
+                                     / pair_roofline_peak(sm_count, mhz, N_FP32_PER_PAIR_ADJOINT),
             "fp64_seconds_per_mesh": sec64, "speedup_vs_fp64": sec64 / (sec / len(dev)),
             "grad_rel_err_vs_fp64": gerr, "dist_rel_err_vs_fp64": abs(out[0].item() - o64.item()) / o64.item()}
     v, t = synth.adjoint_mesh(16, 0)

@@ -85,6 +85,14 @@ struct PreciseSet {
     unsigned char* d_flag = nullptr;    // per node block: 1 if listed
 };
 
+// Lattice (cube) rules: nodes on lines of fixed (eta_y, eta_z) = h (j, k),
+// eta_x = h i for i = i0 .. i0 + count - 1, stored consecutively.
+struct LatLine {
+    float yh, yl, zh, zl;  // eta_y, eta_z (turns per unit length) as float pairs
+    int i0, count;
+    int64_t node0;         // index of the line's first node
+};
+
 struct wd_rule {
     wd_ctx* ctx = nullptr;
     wd_rule_desc desc{};
@@ -104,6 +112,12 @@ struct wd_rule {
     double* d_rad = nullptr;          // radial nodes, n_rad
     float* d_dir = nullptr;           // per direction, SoA 9 * n_dir: omega (x, y, z) in float32,
                                       // then omega / 2 pi as float pairs: high (x, y, z), low (x, y, z)
+    // cube rules: the lattice lines and, per node block of WD_NPB nodes, the
+    // first line it touches and the block's first node's place in that line
+    int64_t n_lines = 0;
+    LatLine* d_lines = nullptr;
+    int2* d_lblk = nullptr;
+    float lat_hh = 0.0f, lat_hl = 0.0f;   // lattice step h as a float pair
     std::map<double, double*> w_cache;                  // s -> W_k
     std::map<double, PreciseSet> precise_cache;         // s -> extended-precision node blocks
     std::map<std::array<double, 4>, double*> nu_cache;  // (radius, center) -> nu^ (re, im interleaved)
@@ -127,7 +141,7 @@ struct wd_ctx {
     std::atomic<int64_t> launches{0};
     // resident blocks of each kernel on this context's device (0: not yet
     // queried); written once per slot, any thread may fill a slot
-    std::atomic<int> occupancy[24] = {};
+    std::atomic<int> occupancy[24] = {};  // OccSlot
 };
 
 // resident-block slots of wd_ctx::occupancy
@@ -138,6 +152,8 @@ enum OccSlot {
     OCC_ADJOINT = 12,      // + 0 float64, 1 mixed, 2 radial (3 slots)
     OCC_PRECISE = 15,      // + mode (3 slots)
     OCC_SERVE_PRECISE = 18,
+    OCC_LATTICE = 19,      // + mode (3 slots)
+    OCC_SERVE_LATTICE = 22,
 };
 // the cached count of slot `slot`, or query(kernel) * SMs stored there
 template <typename K>
@@ -176,6 +192,7 @@ enum PairMode { MODE_DIST = 0, MODE_FT = 1, MODE_RESID = 2 };
 
 struct PairPlan {
     bool radial = false;      // radius x direction node blocks (ball rules, mixed path)
+    bool lattice = false;     // per-node blocks with lattice-line records (cube rules, mixed path)
     int64_t n_dg = 0;         // radial plan: direction groups
     int n_rg = 0;             // radial plan: radius groups
     int64_t n_nodes = 0;
@@ -207,6 +224,9 @@ struct PairArgs {
     int n_rad = 0;
     int64_t n_dir = 0;
     int64_t dith_base = 0;        // radial plan: node index of the window's first node in the full rule
+    const LatLine* lines = nullptr;  // lattice plan: lines, per-block (first line, offset), h
+    const int2* lblk = nullptr;
+    float lat_hh = 0.0f, lat_hl = 0.0f;
     // mixed per-node plan: node blocks evaluated in extended precision (see
     // wd_rule_precise), their chunk partials (wd_precise_partial_bytes)
     const unsigned char* precise_flag = nullptr;  // per node block
@@ -293,13 +313,11 @@ struct ServeRange {         // items [first, first + count) of request `req`
     int64_t first;
     int64_t start;          // launch-local index of the range's first item (prefix sum)
 };
-enum { SERVE_RADIAL = 0, SERVE_NODE = 1, SERVE_PRECISE = 2, SERVE_FORMS = 3 };
+enum { SERVE_RADIAL = 0, SERVE_NODE = 1, SERVE_PRECISE = 2, SERVE_LATTICE = 3, SERVE_FORMS = 4 };
 struct ServeTable {         // laid out in pinned host memory and copied whole per launch
     int n_ranges[SERVE_FORMS];  // per kernel form
-    int pad0;
     int64_t n_items[SERVE_FORMS];
     int next[SERVE_FORMS];  // dynamic item counters (zero in the host copy)
-    int pad1;
 };
 constexpr int WD_SERVE_RANGES = 512;  // ranges per form and launch
 // table layout: ServeTable, then WD_SERVE_RANGES ranges per form, then the requests

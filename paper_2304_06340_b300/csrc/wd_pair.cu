@@ -244,11 +244,15 @@ __device__ __forceinline__ void pair_mixed_divdiff(const TabEntry* __restrict__ 
 // every time, and it has one sign (-p/24), so the loss would be a bias. It is
 // added inside the final rounding with gamma, where gamma c/2 is a full-width
 // product off the float grid.
+// FAST: expm_turns_fast (the lattice kernel's series rows)
+template <bool FAST = false>
 __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab, float tau, float tlo, float sr,
                                                float si, float gam, float gam_lo, float& fr, float& fi, float magic)
 {
     float c, s;
-    expm_turns(tab, tau, tlo, c, s, magic);  // (c, s) = exp(-i (t_m - 2 pi dith + 2 pi shift))
+    // (c, s) = exp(-i (t_m - 2 pi dith + 2 pi shift))
+    if (FAST) expm_turns_fast(tab, tau, tlo, c, s, magic);
+    else expm_turns(tab, tau, tlo, c, s, magic);
     // gamma (c + i s)(1/2 + sr + i si) = g2 (c + i s) + (c + i s)(ar + i ai) with
     // g2 = gamma/2, ar = gamma sr + gamma_lo/2, ai = gamma si; gamma_lo times
     // the tail (2^-24 of a zero-mean term) is left out
@@ -258,6 +262,9 @@ __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab,
     fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
     fi = fmaf(g2, s, fmaf(s, ar, c * ai));
 }
+
+__device__ __forceinline__ void pair_mixed_gaps(const TabEntry* __restrict__ tab, float tau, float tlo, float g1,
+                                                float g2, float gam, float gam_lo, float& fr, float& fi, float magic);
 
 __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, const NodeF& q, const TriRecF& t,
                                            float& fr, float& fi, float magic)
@@ -282,9 +289,17 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
     // rounding of f - dith (below 2^-25 turns) varies pseudo-randomly with the
     // dithered phase and averages out over the triangles
     const float tau = f - q.dith;
-    const float tlo = lo;
     const float g1 = fmaf(q.x, t.e1[0], fmaf(q.y, t.e1[1], q.z * t.e1[2]));
     const float g2 = fmaf(q.x, t.e2[0], fmaf(q.y, t.e2[1], q.z * t.e2[2]));
+    pair_mixed_gaps(tab, tau, lo, g1, g2, t.gam, t.gam_lo, fr, fi, magic);
+}
+
+// F_T from the dithered centroid phase (tau, tlo) in turns and the edge gaps
+// g1, g2: the centred Taylor series below DELTA, else the largest-gap
+// recurrence.
+__device__ __forceinline__ void pair_mixed_gaps(const TabEntry* __restrict__ tab, float tau, float tlo, float g1,
+                                                float g2, float gam, float gam_lo, float& fr, float& fi, float magic)
+{
     const float g3 = g2 - g1;
     const float a1 = fabsf(g1), a2 = fabsf(g2), a3 = fabsf(g3);
     const float gmax = fmaxf(a1, fmaxf(a2, a3));
@@ -320,10 +335,10 @@ __device__ __forceinline__ void pair_mixed(const TabEntry* __restrict__ tab, con
         im = fmaf(im, p, 1.0f / 120.0f);
         const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
         const float si = qq * fmaf(q2, iq, im);
-        taylor_combine(tab, tau, tlo, sr, si, t.gam, t.gam_lo, fr, fi, magic);
+        taylor_combine(tab, tau, tlo, sr, si, gam, gam_lo, fr, fi, magic);
         return;
     }
-    pair_mixed_divdiff(tab, tau, tlo, g1, g2, t.gam, t.gam_lo, fr, fi, magic);
+    pair_mixed_divdiff(tab, tau, tlo, g1, g2, gam, gam_lo, fr, fi, magic);
 }
 
 // ------------------------------------------------------------------ extended-precision per-node pair
@@ -769,6 +784,311 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel_precise(const PairArgs a, 
     }
 }
 
+// ------------------------------------------------------------------ lattice-line kernel (mixed, cube rules)
+// The paper's lattice rule (Sec. 3.2, Eq. (def_trap_grid)) puts its nodes on
+// lines xi = 2 pi (h i, eta_y, eta_z), i = i0 .. i0 + count - 1, stored
+// consecutively. Along a line every per-pair quantity that is linear in xi is
+// affine in i: the centroid phase tau(i) = tau0 + i rho (turns), the gaps
+// g(i) = G + i d, hence A = g1^2 - g1 g2 + g2^2 (= 3p) is quadratic and
+// q = y_a y_b y_c cubic in i. A node block of the per-node plan (256
+// consecutive nodes) touches at most three lines; for each tile of triangles
+// it builds one record per (line, triangle) with these coefficients, and each
+// thread evaluates its pairs from its line's records and its own i.
+//
+// Dither: node i of line L gets d(i) = d0(L) + i delta(L) (mod 1), both on
+// the 2^-20 grid from a hash of L, folded into the record's tau0 and rho, so
+// it costs nothing per pair; the epilogue undoes it as for any node. The
+// phase is the float pair tau0 + i rho with the exact error of the high
+// product kept, as in the radial kernel.
+//
+// Rows (per warp and tile, as in the radial kernel): where every gap the warp
+// meets in the tile is below DELTA_T = 0.6, the centred series to h_6
+// (remainder < 2.1e-9); below DELTA = 3 the series to h_12; else the per-pair
+// choice between the series and the largest-gap recurrence.
+constexpr float kDeltaTiny32 = 0.6f;
+constexpr int LAT_TILE = 64;   // triangles per record tile
+constexpr int LAT_SLOTS = 3;   // lines a node block can touch (lines hold >= WD_NPB / 2 + 1 nodes)
+
+__device__ __forceinline__ uint32_t mix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// the line's dither: d(i) = (d0u + i du) 2^-20 - 1/2 (mod 1)
+__device__ __forceinline__ void line_dither(int64_t L, uint32_t& d0u, uint32_t& du)
+{
+    d0u = mix32((uint32_t)L * 0x9E3779B9u + 0x3C6EF372u) & 0xFFFFFu;
+    du = mix32((uint32_t)L * 0x7F4A7C15u + 0xA54FF53Au) & 0xFFFFFu;
+}
+
+__device__ __forceinline__ float line_node_dither(uint32_t d0u, uint32_t du, int i)
+{
+    return (float)((d0u + (uint32_t)i * du) & 0xFFFFFu) * 9.5367431640625e-7f - 0.5f;  // exact
+}
+
+// Per-(line, triangle) record, grouped by 16 bytes in the order the rows read
+// them: the series rows read groups 0-3, the per-pair rows 0, 1 (gamma), 3, 4.
+struct __align__(16) LatRec {
+    float t0h, t0l;        // dithered phase at i = 0 (turns, reduced mod 1), float pair
+    float rh, rl;          // dithered phase per step of i, float pair
+    float A0, A1, A2;      // A(i) = A0 + A1 i + A2 i^2
+    float gam;             // twice the area, high part (0 for padding)
+    float Q0, Q1, Q2, Q3;  // q(i) = y_a y_b y_c
+    float gam_lo;
+    float gmax;            // bound of the largest |gap| over the block's nodes on this line
+    float pad[2];
+    float G1, d1, G2, d2;  // gaps g1 = G1 + i d1, g2 = G2 + i d2 (radians)
+};
+static_assert(sizeof(LatRec) == 80, "LatRec layout");
+
+__device__ __forceinline__ void make_latrec(const TriRecF& t, const LatLine& ln, int64_t L, float hh, float hl,
+                                            int ia, int ib, LatRec& o)
+{
+    // phase at i = 0 in turns, eta_y m_y + eta_z m_z, in float-pair
+    // arithmetic: exact high products reduced mod 1, two-summed, low terms
+    const float u1 = ln.yh * t.mh[1], u2 = ln.zh * t.mh[2];
+    const float a1 = u1 - rintf(u1), a2 = u2 - rintf(u2);
+    float f = a1 + a2;
+    float lo = two_sum_err(a1, a2, f);
+    lo += fmaf(ln.yh, t.mh[1], -u1) + fmaf(ln.zh, t.mh[2], -u2);
+    lo = fmaf(ln.yh, t.ml[1], lo);
+    lo = fmaf(ln.yl, t.mh[1], lo);
+    lo = fmaf(ln.zh, t.ml[2], lo);
+    lo = fmaf(ln.zl, t.mh[2], lo);
+    uint32_t d0u, du;
+    line_dither(L, d0u, du);
+    const float d0 = (float)d0u * 9.5367431640625e-7f - 0.5f;
+    const float f2 = f - d0;
+    lo += two_sum_err(f, -d0, f2);
+    f = f2 - rintf(f2);
+    o.t0h = f + lo;
+    o.t0l = lo - (o.t0h - f);
+    // rate per step of i: h m_x - du 2^-20
+    const float pr = hh * t.mh[0];
+    float rlo = fmaf(hh, t.mh[0], -pr) + fmaf(hh, t.ml[0], hl * t.mh[0]);
+    const float dd = (float)du * 9.5367431640625e-7f;
+    const float r1 = pr - dd;
+    rlo += two_sum_err(pr, -dd, r1);
+    o.rh = r1 + rlo;
+    o.rl = rlo - (o.rh - r1);
+    // gaps (radians): g = 2 pi (h i e_x + eta_y e_y + eta_z e_z)
+    const float tpi = 6.28318530717958648f;
+    o.G1 = tpi * fmaf(ln.yh, t.e1[1], ln.zh * t.e1[2]);
+    o.d1 = tpi * hh * t.e1[0];
+    o.G2 = tpi * fmaf(ln.yh, t.e2[1], ln.zh * t.e2[2]);
+    o.d2 = tpi * hh * t.e2[0];
+    // A = g1^2 - g1 g2 + g2^2 and q = y_a y_b y_c as polynomials in i
+    o.A2 = fmaf(o.d1, o.d1 - o.d2, o.d2 * o.d2);
+    o.A1 = fmaf(2.0f * o.G1, o.d1, fmaf(2.0f * o.G2, o.d2, -fmaf(o.G1, o.d2, o.G2 * o.d1)));
+    o.A0 = fmaf(o.G1, o.G1 - o.G2, o.G2 * o.G2);
+    const float ya0 = -(o.G1 + o.G2) * (1.0f / 3.0f), ya1 = -(o.d1 + o.d2) * (1.0f / 3.0f);
+    const float yb0 = (2.0f * o.G1 - o.G2) * (1.0f / 3.0f), yb1 = (2.0f * o.d1 - o.d2) * (1.0f / 3.0f);
+    const float yc0 = (2.0f * o.G2 - o.G1) * (1.0f / 3.0f), yc1 = (2.0f * o.d2 - o.d1) * (1.0f / 3.0f);
+    o.Q3 = ya1 * yb1 * yc1;
+    o.Q2 = fmaf(ya0, yb1 * yc1, fmaf(ya1, yb0 * yc1, ya1 * yb1 * yc0));
+    o.Q1 = fmaf(ya0, yb0 * yc1, fmaf(ya0, yb1 * yc0, ya1 * yb0 * yc0));
+    o.Q0 = ya0 * yb0 * yc0;
+    o.gam = t.gam;
+    o.gam_lo = t.gam_lo;
+    // the largest |gap| over i in [ia, ib] (each gap is affine in i)
+    const float fa = (float)ia, fb = (float)ib;
+    const float G3 = o.G2 - o.G1, d3 = o.d2 - o.d1;
+    float gm = fmaxf(fabsf(fmaf(fa, o.d1, o.G1)), fabsf(fmaf(fb, o.d1, o.G1)));
+    gm = fmaxf(gm, fmaxf(fabsf(fmaf(fa, o.d2, o.G2)), fabsf(fmaf(fb, o.d2, o.G2))));
+    gm = fmaxf(gm, fmaxf(fabsf(fmaf(fa, d3, G3)), fabsf(fmaf(fb, d3, G3))));
+    o.gmax = t.gam != 0.0f ? gm : 0.0f;
+    o.pad[0] = o.pad[1] = 0.0f;
+}
+
+struct LatSmem {
+    LatRec rec[LAT_SLOTS][LAT_TILE];
+    TabEntry etab[kTab * kTabRep];
+    unsigned int gmax[LAT_SLOTS * (LAT_TILE / 32)];  // largest gmax of every 32 records, as bits
+    int line[LAT_SLOTS], ia[LAT_SLOTS], ib[LAT_SLOTS];
+    int n_slots;
+};
+
+// Rows: VAR 0 per-pair choice (gaps from G + i d), 1 series to h_12 from
+// A(i), q(i), 2 series to h_6 (every gap below DELTA_T).
+template <int VAR>
+__device__ __forceinline__ void lattice_row(const TabEntry* __restrict__ tl, const LatRec* __restrict__ rec, int cnt4,
+                                            float fi, float magic, Kahan& kr, Kahan& ki)
+{
+    for (int j = 0; j < cnt4; j += 4) {
+        float br = 0.0f, bi = 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const LatRec& t = rec[j + jj];
+            const float P = fi * t.rh;
+            const float lo = fmaf(fi, t.rl, fmaf(fi, t.rh, -P) + t.t0l);
+            const float tau = (P - rintf(P)) + t.t0h;
+            float fr, fim;
+            if (VAR == 0) {
+                pair_mixed_gaps(tl, tau, lo, fmaf(fi, t.d1, t.G1), fmaf(fi, t.d2, t.G2), t.gam, t.gam_lo, fr, fim,
+                                magic);
+            } else {
+                const float A = fmaf(fmaf(t.A2, fi, t.A1), fi, t.A0);
+                const float qq = fmaf(fmaf(fmaf(t.Q3, fi, t.Q2), fi, t.Q1), fi, t.Q0);
+                const float p = A * (1.0f / 3.0f);
+                float sr, si;
+                if (VAR == 2) {
+                    // Psi - 1/2 to h_6: -p/24 + p^2/720 - (p^3 + q^2)/8! + i (q/120 - 2 p q/7!)
+                    const float t2 = fmaf(p * p, fmaf(p, -1.0f / 40320.0f, 1.0f / 720.0f), qq * qq * (-1.0f / 40320.0f));
+                    sr = fmaf(A, -1.388888899e-02f, fmaf(A, 1.034802868e-10f, t2));  // -A (1/72 hi + lo)
+                    si = qq * fmaf(p, -2.0f / 5040.0f, 1.0f / 120.0f);
+                } else {
+                    // to h_12, as in pair_mixed
+                    const float q2 = qq * qq;
+                    float re = fmaf(p, 1.0f / 87178291200.0f, -1.0f / 479001600.0f);
+                    re = fmaf(re, p, 1.0f / 3628800.0f);
+                    re = fmaf(re, p, -1.0f / 40320.0f);
+                    re = fmaf(re, p, 1.0f / 720.0f);
+                    float rq = fmaf(p, 10.0f / 87178291200.0f, -6.0f / 479001600.0f);
+                    rq = fmaf(rq, p, 3.0f / 3628800.0f);
+                    rq = fmaf(rq, p, -1.0f / 40320.0f);
+                    rq = fmaf(q2, 1.0f / 87178291200.0f, rq);
+                    sr = fmaf(re, p * p, q2 * rq);
+                    sr = fmaf(A, -1.388888899e-02f, fmaf(A, 1.034802868e-10f, sr));
+                    float im = fmaf(p, 5.0f / 6227020800.0f, -4.0f / 39916800.0f);
+                    im = fmaf(im, p, 3.0f / 362880.0f);
+                    im = fmaf(im, p, -2.0f / 5040.0f);
+                    im = fmaf(im, p, 1.0f / 120.0f);
+                    const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
+                    si = qq * fmaf(q2, iq, im);
+                }
+                taylor_combine<true>(tl, tau, lo, sr, si, t.gam, t.gam_lo, fr, fim, magic);
+            }
+            br += fr;
+            bi += fim;
+        }
+        kr.add(br);
+        ki.add(bi);
+    }
+}
+
+// One work item (node block nb, triangle chunk) of the lattice form. Called by
+// every thread of the block (barriers inside); etab is filled.
+template <int MODE>
+__device__ __forceinline__ void lattice_item(const PairArgs& a, const PairPlan& p, int64_t nb, int chunk, LatSmem& sm,
+                                             double* red, int& s_last)
+{
+    const int64_t n = a.n;
+    const int64_t node = nb * WD_NPB + threadIdx.x;
+    const bool active = node < n;
+    // the block's lines: slot s is line lblk.x + s over the block's nodes
+    const int2 bd = a.lblk[nb];
+    __syncthreads();  // the previous item is done with sm
+    if (threadIdx.x == 0) {
+        const int64_t last = (n - nb * WD_NPB) < WD_NPB ? n - nb * WD_NPB : WD_NPB;  // nodes in the block
+        int64_t L = bd.x, pos = bd.y, left = last;
+        int ns = 0;
+        while (left > 0 && ns < LAT_SLOTS) {
+            const LatLine ln = a.lines[L];
+            const int64_t take = (ln.count - pos) < left ? (ln.count - pos) : left;
+            sm.line[ns] = (int)L;
+            sm.ia[ns] = ln.i0 + (int)pos;
+            sm.ib[ns] = ln.i0 + (int)(pos + take - 1);
+            ++ns;
+            left -= take;
+            pos = 0;
+            ++L;
+        }
+        sm.n_slots = ns;
+    }
+    __syncthreads();
+    // this thread's slot and i
+    int slot = 0, i = 0;
+    {
+        int pos = threadIdx.x;
+        for (int s = 0; s < sm.n_slots; ++s) {
+            const int len = sm.ib[s] - sm.ia[s] + 1;
+            if (pos < len || s == sm.n_slots - 1) {
+                slot = s;
+                i = sm.ia[s] + pos;
+                break;
+            }
+            pos -= len;
+        }
+    }
+    uint32_t d0u = 0, du = 0;
+    line_dither(sm.line[slot], d0u, du);
+    const float dith = line_node_dither(d0u, du, i);
+    const float fi = (float)i;
+    const TabEntry* tl = exp_table_lane(sm.etab);
+    // slots of the warp's first and last active lane (a warp spans at most two lines)
+    const int s_lo = __reduce_min_sync(0xffffffffu, active ? slot : LAT_SLOTS);
+    const int s_hi = __reduce_max_sync(0xffffffffu, active ? slot : 0);
+
+    double acc_r = 0.0, acc_i = 0.0;
+    const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
+    int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
+    if (t1 > a.T) t1 = a.T;
+    const TriRecF* tris = static_cast<const TriRecF*>(a.tris);
+    for (int64_t tb = t0; tb < t1; tb += LAT_TILE) {
+        const int cnt = (int)((t1 - tb) < LAT_TILE ? (t1 - tb) : LAT_TILE);
+        const int cnt4 = (cnt + 3) & ~3;
+        __syncthreads();
+        for (int k = threadIdx.x; k < LAT_SLOTS * LAT_TILE; k += WD_NPB) {
+            const int sl = k / LAT_TILE, j = k % LAT_TILE;
+            float gm = 0.0f;
+            if (sl < sm.n_slots && j < cnt4) {
+                LatRec o;
+                if (j < cnt) {
+                    make_latrec(tris[tb + j], a.lines[sm.line[sl]], sm.line[sl], a.lat_hh, a.lat_hl, sm.ia[sl],
+                                sm.ib[sl], o);
+                } else {
+                    o = LatRec{};
+                }
+                gm = o.gmax;
+                sm.rec[sl][j] = o;
+            }
+            const unsigned int wm = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
+            if ((threadIdx.x & 31) == 0) sm.gmax[k / 32] = wm;
+        }
+        __syncthreads();
+        if (s_lo > s_hi) continue;  // no active lane in this warp (warp-uniform)
+        unsigned int gu = 0u;
+        for (int s = s_lo; s <= s_hi; ++s)
+            for (int part = 0; part < LAT_TILE / 32; ++part) gu = max(gu, sm.gmax[s * (LAT_TILE / 32) + part]);
+        const float gap_row = __uint_as_float(gu);
+        // the node's per-tile phase shift in whole table steps, undone in float64
+        const int shift = tile_shift(node, tb / LAT_TILE);
+        const float magic = kMagic + (float)shift;
+        Kahan kr, ki;
+        const LatRec* rec = sm.rec[slot];
+        if (gap_row < kDeltaTiny32)
+            lattice_row<2>(tl, rec, cnt4, fi, magic, kr, ki);
+        else if (gap_row < kDelta32)
+            lattice_row<1>(tl, rec, cnt4, fi, magic, kr, ki);
+        else
+            lattice_row<0>(tl, rec, cnt4, fi, magic, kr, ki);
+        unshift_add(sm.etab, shift, kr.value(), ki.value(), acc_r, acc_i);
+    }
+    const PartialSlots ps{a.partial, a.n};
+    node_epilogue<true, MODE, 1>(a, p, nb, chunk, &node, &active, &dith, &acc_r, &acc_i, red, s_last, ps, &node);
+}
+
+// The lattice form over every node block, skipping the blocks that the
+// extended-precision kernel takes.
+template <int MODE>
+__global__ void __launch_bounds__(WD_NPB) pair_kernel_lattice(const PairArgs a, const PairPlan p)
+{
+    __shared__ __align__(16) LatSmem sm;
+    __shared__ double red[WD_NPB / 32];
+    __shared__ int s_last;
+    fill_exp_table(sm.etab);  // visible after the first barrier
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const int64_t nb = item / p.nchunks;
+        if (a.precise_flag && a.precise_flag[nb]) continue;  // block-uniform
+        lattice_item<MODE>(a, p, nb, (int)(item - nb * p.nchunks), sm, red, s_last);
+    }
+}
+
 // ------------------------------------------------------------------ radial pair kernel (mixed, ball rules)
 // Ball-rule nodes factor as xi = r omega (radius r, unit direction omega), so
 // every per-pair quantity that is linear in xi is a per-(direction, triangle)
@@ -912,7 +1232,7 @@ __device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__
                                                     float magic)
 {
     float c, s;
-    expm_turns(tl, tau, tlo, c, s, magic);
+    expm_turns_fast(tl, tau, tlo, c, s, magic);
     fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
     fi = fmaf(g2, s, fmaf(s, ar, c * ai));
 }
@@ -1077,8 +1397,10 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
         if ((threadIdx.x & 31) == 0) s_rmax[threadIdx.x >> 5] = __uint_as_float(u);  // read after a barrier
     }
     const TabEntry* tl = exp_table_lane(tab);
-#pragma unroll
-    for (int q = 0; q < WD_RAD_RPT; ++q) acc_r[q] = acc_i[q] = 0.0;
+    // one compensated float32 sum per node over the whole triangle range (the
+    // pair (s, c) goes to float64 once, at the end: a float64 conversion per
+    // tile kept this GPU's narrow float64 pipe 10 % busy)
+    Kahan kr[WD_RAD_RPT], ki[WD_RAD_RPT];
     for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
         const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
         const int cnt8 = (cnt + 7) & ~7;
@@ -1105,7 +1427,10 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
             if ((threadIdx.x & 31) == 0) s_gmax[i / 32] = wm;
         }
         __syncthreads();
-        if (!h.dir_ok) continue;  // warp-uniform
+        bool any_node = false;
+#pragma unroll
+        for (int q = 0; q < WD_RAD_RPT; ++q) any_node = any_node || h.active[q];
+        if (!h.dir_ok || !__any_sync(0xffffffffu, any_node)) continue;  // warp-uniform: no node here
         const RadRec* rec = tile[h.dl];
         // No per-tile phase shift here: on ball rules the weight spreads over
         // many nodes and the shift's float64 rotation cost 3% of the
@@ -1118,18 +1443,17 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
 #pragma unroll
         for (int p = 0; p < kParts; ++p) gu = max(gu, s_gmax[h.dl * kParts + p]);
         const float gap_row = __uint_as_float(gu) * s_rmax[threadIdx.x >> 5];  // bounds every lane's gaps
-        Kahan kr[WD_RAD_RPT], ki[WD_RAD_RPT];
         if (gap_row < kDeltaShort32)
             radial_row<2>(tl, rec, cnt8, h, kr, ki);
         else if (gap_row < kDelta32)
             radial_row<1>(tl, rec, cnt8, h, kr, ki);
         else
             radial_row<0>(tl, rec, cnt8, h, kr, ki);
+    }
 #pragma unroll
-        for (int q = 0; q < WD_RAD_RPT; ++q) {
-            acc_r[q] += kr[q].value();
-            acc_i[q] += ki[q].value();
-        }
+    for (int q = 0; q < WD_RAD_RPT; ++q) {
+        acc_r[q] = kr[q].value();
+        acc_i[q] = ki[q].value();
     }
 }
 
@@ -1173,6 +1497,19 @@ template <bool MIXED, int MODE>
 int resident_blocks(wd_ctx* ctx)
 {
     return wd_resident(ctx, OCC_PAIR + 3 * (MIXED ? 1 : 0) + MODE, pair_kernel<MIXED, MODE>, WD_NPB);
+}
+
+template <int MODE>
+int resident_lattice(wd_ctx* ctx)
+{
+    return wd_resident(ctx, OCC_LATTICE + MODE, pair_kernel_lattice<MODE>, WD_NPB);
+}
+
+int resident_lattice_for(wd_ctx* ctx, int mode)
+{
+    if (mode == MODE_FT) return resident_lattice<MODE_FT>(ctx);
+    if (mode == MODE_RESID) return resident_lattice<MODE_RESID>(ctx);
+    return resident_lattice<MODE_DIST>(ctx);
 }
 
 template <int MODE>
@@ -1307,6 +1644,31 @@ __global__ void __launch_bounds__(WD_NPB) serve_kernel_node(ServeTable* __restri
     }
 }
 
+// Requests with a lattice plan (mixed path, cube rules): the lattice form.
+__global__ void __launch_bounds__(WD_NPB) serve_kernel_lattice(ServeTable* __restrict__ head,
+                                                               const ServeRange* __restrict__ ranges,
+                                                               const ServeReq* __restrict__ reqs)
+{
+    __shared__ __align__(16) LatSmem sm;
+    __shared__ double red[WD_NPB / 32];
+    __shared__ int s_last, s_item;
+    const int64_t n_items = head->n_items[SERVE_LATTICE];
+    if (n_items == 0) return;
+    fill_exp_table(sm.etab);
+    const ServeRange* rg = ranges + 3 * WD_SERVE_RANGES;
+    const int n_rg = head->n_ranges[SERVE_LATTICE];
+    for (;;) {
+        const int64_t it = serve_next_item(&head->next[SERVE_LATTICE], &s_item);
+        if (it >= n_items) break;
+        const ServeRange& r = serve_find_range(rg, n_rg, it);
+        const ServeReq& rq = reqs[r.req];
+        const int64_t item = r.first + (it - r.start);
+        const int64_t nb = item / rq.p.nchunks;
+        if (rq.a.precise_flag && rq.a.precise_flag[nb]) continue;  // the precise form's block
+        lattice_item<MODE_DIST>(rq.a, rq.p, nb, (int)(item - nb * rq.p.nchunks), sm, red, s_last);
+    }
+}
+
 // The extended-precision blocks of requests with a mixed per-node plan: item
 // i of a request is chunk i mod pp.nchunks of its listed block i / pp.nchunks.
 __global__ void __launch_bounds__(WD_NPB) serve_kernel_precise(ServeTable* __restrict__ head,
@@ -1374,6 +1736,17 @@ wd_status wd_plan_pair(wd_ctx* ctx, int precision, int mode, int64_t n_nodes, in
 wd_status wd_plan_pair_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int mode, int64_t n_tris,
                             PairPlan* plan)
 {
+    if (precision == WD_MIXED && rule->d_lines) {
+        // lattice rules: the per-node blocks, evaluated with line records
+        PairPlan p;
+        p.lattice = true;
+        p.n_nodes = rule->n_eval;
+        p.n_tris = n_tris;
+        p.n_nb = (rule->n_eval + WD_NPB - 1) / WD_NPB;
+        plan_chunks(p, resident_lattice_for(ctx, mode));
+        *plan = p;
+        return WD_OK;
+    }
     if (precision != WD_MIXED || !rule->d_rad || rule->n_dir <= 0)
         return wd_plan_pair(ctx, precision, mode, rule->n_eval, n_tris, plan);
     PairPlan p;
@@ -1422,6 +1795,10 @@ void wd_pair_args_rule(const wd_rule* rule, PairArgs& a)
     a.n_rad = rule->n_rad;
     a.n_dir = rule->n_dir;
     a.dith_base = (int64_t)rule->shell0 * rule->n_dir;
+    a.lines = rule->d_lines;
+    a.lblk = rule->d_lblk;
+    a.lat_hh = rule->lat_hh;
+    a.lat_hl = rule->lat_hl;
 }
 
 wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
@@ -1437,9 +1814,21 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
         else if (mode == MODE_RESID) pair_kernel_radial<MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
         else pair_kernel_radial<MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
     } else if (precision == WD_MIXED) {
-        if (mode == MODE_FT) pair_kernel<true, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
-        else if (mode == MODE_RESID) pair_kernel<true, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
-        else pair_kernel<true, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        if (plan.lattice) {
+            if (!args.lines || !args.lblk) {
+                wd_set_error("internal: lattice plan without the rule's lines");
+                return WD_EINVAL;
+            }
+            if (mode == MODE_FT) pair_kernel_lattice<MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+            else if (mode == MODE_RESID) pair_kernel_lattice<MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+            else pair_kernel_lattice<MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        } else if (mode == MODE_FT) {
+            pair_kernel<true, MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        } else if (mode == MODE_RESID) {
+            pair_kernel<true, MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        } else {
+            pair_kernel<true, MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        }
         if (args.n_precise > 0) {
             WD_CUDA(cudaGetLastError());
             ctx->launches++;
@@ -1466,6 +1855,7 @@ int wd_serve_resident(wd_ctx* ctx, int precision, int form)
 {
     if (form == SERVE_RADIAL) return wd_resident(ctx, OCC_SERVE, serve_kernel_radial, WD_NPB);
     if (form == SERVE_PRECISE) return wd_resident(ctx, OCC_SERVE_PRECISE, serve_kernel_precise, WD_NPB);
+    if (form == SERVE_LATTICE) return wd_resident(ctx, OCC_SERVE_LATTICE, serve_kernel_lattice, WD_NPB);
     return precision == WD_MIXED ? wd_resident(ctx, OCC_SERVE + 2, serve_kernel_node<true>, WD_NPB)
                                  : wd_resident(ctx, OCC_SERVE + 1, serve_kernel_node<false>, WD_NPB);
 }
@@ -1497,11 +1887,14 @@ wd_status wd_launch_serve(wd_ctx* ctx, int precision, ServeTable* d_head, const 
         WD_CUDA(cudaGetLastError());
         serve_kernel_precise<<<wd_serve_resident(ctx, precision, SERVE_PRECISE), WD_NPB, 0, st>>>(d_head, d_ranges,
                                                                                                 d_reqs);
+        WD_CUDA(cudaGetLastError());
+        serve_kernel_lattice<<<wd_serve_resident(ctx, precision, SERVE_LATTICE), WD_NPB, 0, st>>>(d_head, d_ranges,
+                                                                                                d_reqs);
     } else {
         serve_kernel_node<false><<<wd_serve_resident(ctx, precision, SERVE_NODE), WD_NPB, 0, st>>>(d_head, d_ranges,
                                                                                                  d_reqs);
     }
     WD_CUDA(cudaGetLastError());
-    ctx->launches += precision == WD_MIXED ? 3 : 1;
+    ctx->launches += precision == WD_MIXED ? 4 : 1;
     return WD_OK;
 }

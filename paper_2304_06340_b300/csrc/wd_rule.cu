@@ -126,6 +126,8 @@ void release_rule(wd_rule* r)
     cudaFree(r->d_wg);
     cudaFree(r->d_rad);
     cudaFree(r->d_dir);
+    cudaFree(r->d_lines);
+    cudaFree(r->d_lblk);
     for (auto& kv : r->w_cache) cudaFree(kv.second);
     for (auto& kv : r->precise_cache) {
         cudaFree(kv.second.d_list);
@@ -328,13 +330,58 @@ static wd_status build_cube_rule(wd_ctx* ctx, const wd_rule_desc* d, wd_rule** o
                 r->h_wg[k] = (double)(h * h * h * fx * fy * fz * ((herm && !origin) ? 2.0L : 1.0L));
                 ++k;
             }
+    // the lattice lines (fixed j, k) in node order, and each node block's first
+    // line; with full lines of 2m + 1 >= WD_NPB / 2 + 1 nodes a block of WD_NPB
+    // consecutive nodes touches at most three lines (the one half line of a
+    // Hermitian rule comes first), which the lattice kernel relies on; for
+    // smaller M the per-node kernel serves the rule
+    const bool lattice = 2 * m + 1 >= WD_NPB / 2 + 1;
+    std::vector<LatLine> lines;
+    for (int iz = herm ? 0 : -m; iz <= m && lattice; ++iz)
+        for (int iy = -m; iy <= m; ++iy) {
+            if (herm && iz == 0 && iy < 0) continue;
+            LatLine ln;
+            const long double ey = h * iy, ez = h * iz;
+            ln.yh = (float)ey;
+            ln.yl = (float)(ey - (long double)ln.yh);
+            ln.zh = (float)ez;
+            ln.zl = (float)(ez - (long double)ln.zh);
+            ln.i0 = (herm && iz == 0 && iy == 0) ? 0 : -m;
+            ln.count = m - ln.i0 + 1;
+            ln.node0 = lines.empty() ? 0 : lines.back().node0 + lines.back().count;
+            lines.push_back(ln);
+        }
+    const int64_t n_nb = lattice ? (n + WD_NPB - 1) / WD_NPB : 0;
+    std::vector<int2> lblk(n_nb > 0 ? n_nb : 1);
+    for (int64_t b = 0, L = 0; b < n_nb; ++b) {
+        const int64_t node = b * WD_NPB;
+        while (node >= lines[L].node0 + lines[L].count) ++L;
+        lblk[b] = make_int2((int)L, (int)(node - lines[L].node0));
+    }
+    r->n_lines = (int64_t)lines.size();
+    r->lat_hh = (float)h;
+    r->lat_hl = (float)(h - (long double)r->lat_hh);
     st = upload_rule(ctx, r);
+    if (st == WD_OK && lattice) {
+        if (wd_dev_alloc(&r->d_lines, sizeof(LatLine) * lines.size(), "lattice lines") != cudaSuccess ||
+            wd_dev_alloc(&r->d_lblk, sizeof(int2) * lblk.size(), "lattice block lines") != cudaSuccess) {
+            cudaGetLastError();
+            wd_set_error("out of device memory for the lattice lines");
+            st = WD_ENOMEM;
+        } else if (cudaMemcpy(r->d_lines, lines.data(), sizeof(LatLine) * lines.size(), cudaMemcpyHostToDevice) !=
+                       cudaSuccess ||
+                   cudaMemcpy(r->d_lblk, lblk.data(), sizeof(int2) * lblk.size(), cudaMemcpyHostToDevice) !=
+                       cudaSuccess) {
+            st = wd_cuda_status(cudaGetLastError(), "lattice line upload");
+        }
+    }
     if (st != WD_OK) {
         release_rule(r);
         return st;
     }
     ctx->rules.push_back(r);
-    wd_log(3, "cube rule xi_max=%g M=%d hermitian=%d: %lld nodes", d->R, d->n_r, key.hermitian, (long long)n);
+    wd_log(3, "cube rule xi_max=%g M=%d hermitian=%d: %lld nodes on %lld lines", d->R, d->n_r, key.hermitian,
+           (long long)n, (long long)r->n_lines);
     *out = r;
     return WD_OK;
 }

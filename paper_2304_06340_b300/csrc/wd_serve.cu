@@ -355,8 +355,8 @@ int64_t build_launch(wd_server* sv, int b, int64_t seq, double* pairs_out)
             progress = true;
         }
     }
-    int n_rg[SERVE_FORMS] = {0, 0, 0};
-    int64_t n_it[SERVE_FORMS] = {0, 0, 0};
+    int n_rg[SERVE_FORMS] = {0, 0, 0, 0};
+    int64_t n_it[SERVE_FORMS] = {0, 0, 0, 0};
     auto add_range = [&](int f, int slot, int64_t first, int64_t count) {
         ServeRange& g = ranges[f * WD_SERVE_RANGES + n_rg[f]++];
         g.req = slot;
@@ -373,7 +373,7 @@ int64_t build_launch(wd_server* sv, int b, int64_t seq, double* pairs_out)
             add_range(SERVE_RADIAL, r->slot, a, e - a);
         } else {
             const int64_t m = r->plan.n_items;  // plain items [0, m), then the precise ones
-            if (a < m) add_range(SERVE_NODE, r->slot, a, std::min(e, m) - a);
+            if (a < m) add_range(r->plan.lattice ? SERVE_LATTICE : SERVE_NODE, r->slot, a, std::min(e, m) - a);
             if (e > m) add_range(SERVE_PRECISE, r->slot, std::max(a, m) - m, e - std::max(a, m));
         }
         r->next_item = e;
@@ -386,7 +386,7 @@ int64_t build_launch(wd_server* sv, int b, int64_t seq, double* pairs_out)
         head->next[f] = 0;
     }
     *pairs_out = pairs;
-    return n_it[0] + n_it[1] + n_it[2];
+    return n_it[0] + n_it[1] + n_it[2] + n_it[3];
 }
 
 // Retire launch `seq` (complete on the device): deliver the queries it

@@ -130,3 +130,35 @@ def test_extended_precision_blocks_follow_the_weight(ctx):
         d_or = oracle.distance(xo, wo, s, v, t, wscale=oracle.PAPER_WSCALE)
         dmx = ctx.distance(rule, v, t, None, s, wd.WD_MIXED)
         assert dmx == pytest.approx(d_or, rel=1e-7), (s, (dmx - d_or) / d_or)
+
+
+def test_lattice_kernel_transform_matches_oracle(ctx):
+    """The lattice-line form (mixed, cube rules with M >= 128) per node against
+    the oracle at sampled nodes: T_1 (large gaps: per-pair rows with the
+    largest-gap recurrence) and T_5 (small gaps: the series rows), including
+    the origin and the boundary lines."""
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    xi, _ = wd.wd_rule_copy_nodes(rule)
+    rng = np.random.default_rng(5)
+    idx = np.concatenate([[0, 1, 64, 65, 194, len(xi) - 1], rng.choice(len(xi), 58, replace=False)])
+    for N in (1, 5):
+        v, t = synth.icosphere_recursive(N)
+        v = synth.jitter_isotropic(v, 1e-3, N)
+        mu = wd.wd_mesh_ft(ctx.handle, rule, v, t, wd.WD_MIXED)
+        want = oracle.mesh_ft(v, t, xi[idx])
+        area = 0.5 * np.linalg.norm(np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]]), axis=1).sum()
+        err = np.abs(mu[idx] - want).max() / area
+        assert err < 1e-7, (N, err)
+
+
+@pytest.mark.parametrize("N, s", [(0, 10.0), (1, 3.0), (2, 10.0)])
+def test_lattice_kernel_distance_matches_oracle(ctx, N, s):
+    """D on the paper's full M = 128 rule (1,073,345 nodes): for s = 3 most
+    node blocks run the lattice form (weights within 1e-3 of the largest only
+    for |eta| < 3), for s = 10 all but the blocks near the origin."""
+    v, t = synth.icosphere_recursive(N)
+    xo, wo = oracle.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    d_or = oracle.distance(xo, wo, s, v, t, wscale=oracle.PAPER_WSCALE)
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    dmx = ctx.distance(rule, v, t, None, s, wd.WD_MIXED)
+    assert dmx == pytest.approx(d_or, rel=1e-7), (dmx - d_or) / d_or

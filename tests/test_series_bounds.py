@@ -5,9 +5,10 @@ For vertex phases t_a, t_b, t_c with centroid t_m and centred phases
 y = t - t_m, F_T = gamma exp(-i t_m) Psi(y) with
 Psi(y) = sum_n (-i)^n h_n(y) / (n+2)!, h_n the complete homogeneous symmetric
 polynomial of degree n. The kernels keep n <= 12 while the largest gap is
-below 3, and the radial kernel keeps n <= 9 for whole rows whose largest gap
-is below 1.5. The exact Psi comes from the oracle's long-double transform of
-one triangle whose phases are the x coordinates of its vertices (xi = e_x).
+below 3, the radial kernel keeps n <= 9 for whole rows whose largest gap is
+below 1.5, and the lattice kernel keeps n <= 6 for whole rows whose largest
+gap is below 0.6. The exact Psi comes from the oracle's long-double transform
+of one triangle whose phases are the x coordinates of its vertices (xi = e_x).
 """
 import math
 
@@ -26,7 +27,7 @@ def psi_truncated(y, n_max):
     return sum((-1j) ** n * h(n, y) / math.factorial(n + 2) for n in range(n_max + 1))
 
 
-@pytest.mark.parametrize("gap, n_max, bound", [(1.5, 9, 1.1e-9), (3.0, 12, 3.2e-9)])
+@pytest.mark.parametrize("gap, n_max, bound", [(0.6, 6, 2.1e-9), (1.5, 9, 1.1e-9), (3.0, 12, 3.2e-9)])
 def test_centred_series_remainder_below_the_kernel_bound(gap, n_max, bound):
     rng = np.random.default_rng(7)
     worst = 0.0
