@@ -45,10 +45,13 @@ N_MUFU_PER_PAIR = 6
 # (Taylor branch): FP32 pipe operations
 N_FP32_PER_PAIR_ADJOINT = 80
 L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
-# DRAM bytes (read + write) of one launch of the radial pair kernel on the
-# large query, from an ncu capture of the current kernel; None when the kernel
-# has changed since the capture.
-PAIR_KERNEL_TRAFFIC_LARGE = None
+# From ncu captures of the current radial pair kernel (set to None when the
+# kernel changes): DRAM bytes (read + write) of one large-query launch, and the
+# thread instructions per pair and issue-active fraction of its full-set
+# capture on a 64-shell window of the same rule.
+PAIR_KERNEL_TRAFFIC_LARGE = 129.71e6 + 6.37e6
+PAIR_KERNEL_INSTR_PER_PAIR = 56.2
+PAIR_KERNEL_ISSUE_ACTIVE = 0.771
 # radial shells of the large rule whose D is recomputed in float64 after the
 # timed region (a 32-aligned window evaluates every node with the same float32
 # operations as the full launch)
@@ -75,7 +78,7 @@ def parse():
     p.add_argument("--case", choices=["adjoint-n16", "large-window", "large"], default=None,
                    help="run one fixed case for a profiler and exit: adjoint-n16 = three mixed gradients of the "
                         "n=16 adjoint-configuration mesh (seed 0) on the 192x64x96 rule; large-window = two "
-                        "mixed distances of the large query on radial shells 128-159 of its rule; large = two "
+                        "mixed distances of the large query on radial shells 128-191 of its rule; large = two "
                         "mixed distances of the large query")
     return p.parse_args()
 
@@ -619,7 +622,7 @@ def profile_case(name):
         if name == "large":
             rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
         else:
-            rule = ctx.rule_shells(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian, 128, 160)
+            rule = ctx.rule_shells(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian, 128, 192)
         v, t = synth.large_mesh()
         dv, dt = torch.tensor(v, device="cuda"), torch.tensor(t, device="cuda")
         out = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -778,10 +781,12 @@ def main():
             "frac": pair_rate / peak,
             "frac_at_45_fp32_ops": pair_rate / pair_roofline_peak(sm_count, peaks.get("sm_max_mhz", 2032.0), 45),
             "traffic": PAIR_KERNEL_TRAFFIC_LARGE if large else None,
-            "traffic_note": "dram read+write bytes of one large-query launch of pair_kernel_radial from an ncu "
-                            "capture of the current kernel (null when the kernel changed after it); algorithmic "
-                            "bytes of that launch: W and nu^ per node (24 B x 4,194,304) + mesh records "
-                            "(64 B x 327,680) = 121.6 MB",
+            "measured_instructions_per_pair": PAIR_KERNEL_INSTR_PER_PAIR if large else None,
+            "measured_issue_active": PAIR_KERNEL_ISSUE_ACTIVE if large else None,
+            "traffic_note": "dram read+write bytes of one large-query launch of pair_kernel_radial (ncu, 1-pass "
+                            "metrics, the current kernel); algorithmic bytes of that launch: W and nu^ per node "
+                            "(24 B x 4,194,304) + mesh records (64 B x 327,680) = 121.6 MB; instructions per pair "
+                            "and issue from the full-set capture of the same kernel on shells 128-191",
             "kernel": "pair_kernel_radial (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
             "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
                           % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
