@@ -661,116 +661,9 @@ static_assert(sizeof(AdjRec) % 16 == 0, "AdjRec layout");
 // l, l + 32, ... of the direction, so the Taylor / largest-gap choice, which
 // moves with r, splits a warp at most once per record. Each lane combines its
 // partial sums into the direction's four results with the record's
-// warp-uniform constants, and a warp reduction gives them to every lane.
-// Each warp owns ADJ_RW consecutive triangles of the block's tile for the
-// whole item: per direction its first lanes build those triangles' records,
-// then the warp runs them one after another and adds each result, times
-// omega, to the triangle's float64 totals in its own shared memory. The warps
-// share only the radius table, so the direction loop has no block barrier.
-constexpr int ADJ_RW = ADJ_TT / (ADJ_TPB / 32);  // triangles per warp
-
-// the four results (T0, Ti, T1, T2) of one (direction, triangle) record at
-// the radii of this lane; summed over the warp
-__device__ __forceinline__ float4 adj_dir_tri(const TabEntry* __restrict__ tl, const AdjRec& rc,
-                                              const AdjRad* __restrict__ rt, const float4* __restrict__ ndd,
-                                              int n_rad, int lane)
-{
-    const AdjDirTri& q = rc.q;
-    float S0h = 0.0f, S0t = 0.0f, Sih = 0.0f, Sit = 0.0f, SA = 0.0f, SB = 0.0f;
-    float xP = 0.0f, yP = 0.0f, xQ = 0.0f, yQ = 0.0f, G0 = 0.0f;
-    for (int ir = lane; ir < n_rad; ir += 32) {
-        const AdjRad a = rt[ir];
-        const float4 w = __ldg(ndd + ir);
-        const float rr = w.x, ri = w.y;
-        const float P = a.rh * q.dmh;
-        const float e = fmaf(a.rh, q.dmh, -P);
-        const float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
-        const float tau = (P - rintf(P)) - w.z;
-        if (q.gmax0 < a.thr) {
-            float c, s;
-            expm_turns(tl, tau, lo, c, s);
-            const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
-            const float rho = a.rho, r3 = a.r3;
-            float sr = fmaf(fmaf(fmaf(fmaf(q.R[5], rho, q.R[4]), rho, q.R[3]), rho, q.R[2]), rho, q.R[1]);
-            sr = fmaf(sr, rho, q.R[0]) * rho;
-            float si = fmaf(fmaf(fmaf(q.I[4], rho, q.I[3]), rho, q.I[2]), rho, q.I[1]);
-            si = fmaf(si, rho, q.I[0]) * r3;
-            S0h += Zr;
-            S0t = fmaf(Zr, sr, fmaf(-Zi, si, S0t));
-            Sih = fmaf(Zi, a.rh, Sih);
-            Sit = fmaf(fmaf(Zr, si, Zi * sr), a.rh, Sit);
-            float Ap = fmaf(fmaf(fmaf(fmaf(q.a[4], rho, q.a[3]), rho, q.a[2]), rho, q.a[1]), rho, q.a[0]);
-            Ap = fmaf(Ap, rho, -1.0f / 24.0f);
-            const float Bp = fmaf(fmaf(fmaf(q.b[3], rho, q.b[2]), rho, q.b[1]), rho, q.b[0]) * r3;
-            const float Cq = fmaf(fmaf(fmaf(q.c[3], rho, q.c[2]), rho, q.c[1]), rho, q.c[0]) * r3;
-            float Eq = fmaf(fmaf(fmaf(q.e[3], rho, q.e[2]), rho, q.e[1]), rho, q.e[0]);
-            Eq = fmaf(Eq, rho, 1.0f / 120.0f);
-            SA = fmaf(rho, fmaf(Zr, Ap, -Zi * Bp), SA);
-            SB = fmaf(r3, fmaf(Zr, Cq, -Zi * Eq), SB);
-        } else {
-            float cP, sP, cQ, sQ;
-            expm_turns(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
-            expm_turns(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
-            float scP, dscP, scQ, dscQ;
-            sincd32(a.rh * q.hP0, scP, dscP);
-            sincd32(a.rh * q.hQ0, scQ, dscQ);
-            // X = E sinc(h), Y = i E sinc'(h); x = Re(conj r' X), y = Re(conj r' Y)
-            const float XPr = cP * scP, XPi = sP * scP, XQr = cQ * scQ, XQi = sQ * scQ;
-            xP = fmaf(rr, XPr, fmaf(ri, XPi, xP));
-            xQ = fmaf(rr, XQr, fmaf(ri, XQi, xQ));
-            yP = fmaf(dscP, fmaf(ri, cP, -rr * sP), yP);
-            yQ = fmaf(dscQ, fmaf(ri, cQ, -rr * sQ), yQ);
-            // Re(conj r' i (X_P - X_Q)) / r
-            G0 = fmaf(fmaf(ri, XPr - XQr, -rr * (XPi - XQi)), a.rinv, G0);
-        }
-    }
-    // this lane's share of sum_r rho_0, sum_r rho_i r, sum_r rho_1 r, sum_r rho_2 r
-    const float g1d = rc.d1, g2d = rc.d2;
-    const float ya = -(g1d + g2d) * (1.0f / 3.0f);
-    const float yb = (2.0f * g1d - g2d) * (1.0f / 3.0f);
-    const float yc = (2.0f * g2d - g1d) * (1.0f / 3.0f);
-    const float dq1 = (-yb * yc + 2.0f * ya * yc - ya * yb) * (1.0f / 3.0f);
-    const float dq2 = (-yb * yc - ya * yc + 2.0f * ya * yb) * (1.0f / 3.0f);
-    float T0 = fmaf(0.5f, S0h, S0t);
-    float Ti = fmaf(0.5f, Sih, Sit) * (1.0f / 3.0f);
-    float T1 = fmaf(yb, SA, dq1 * SB);
-    float T2 = fmaf(yc, SA, dq2 * SB);
-    if (q.gmax0 > 0.0f) {  // warp-uniform; with gmax0 = 0 no radius takes the largest-gap branch
-        const float g3d = g2d - g1d;
-        const float a1 = fabsf(g1d), a2 = fabsf(g2d), a3 = fabsf(g3d);
-        const bool caseA = (a2 >= a1) && (a2 >= a3);
-        const bool caseB = !caseA && (a1 >= a3);
-        float oP1, oP2, hP1, hP2, oQ1, oQ2, hQ1, hQ2, D0, D1, D2;
-        if (caseA) {
-            oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
-            oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
-            D0 = g2d; D1 = 0.0f; D2 = 1.0f;
-        } else if (caseB) {
-            oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
-            oQ1 = -1.0f / 3; oQ2 = 1.0f / 6; hQ1 = 0.0f; hQ2 = 0.5f;
-            D0 = g1d; D1 = 1.0f; D2 = 0.0f;
-        } else {
-            oP1 = -1.0f / 3; oP2 = 1.0f / 6; hP1 = 0.0f; hP2 = 0.5f;
-            oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
-            D0 = g3d; D1 = -1.0f; D2 = 1.0f;
-        }
-        const float iD = 1.0f / D0;
-        const float G0D = G0 * iD;
-        T0 += G0D;
-        Ti = fmaf(xP - xQ, iD * (1.0f / 3.0f), Ti);
-        T1 += fmaf(oP1 * xP + hP1 * yP - oQ1 * xQ - hQ1 * yQ, iD, -D1 * G0D * iD);
-        T2 += fmaf(oP2 * xP + hP2 * yP - oQ2 * xQ - hQ2 * yQ, iD, -D2 * G0D * iD);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        T0 += __shfl_xor_sync(0xffffffffu, T0, o);
-        Ti += __shfl_xor_sync(0xffffffffu, Ti, o);
-        T1 += __shfl_xor_sync(0xffffffffu, T1, o);
-        T2 += __shfl_xor_sync(0xffffffffu, T2, o);
-    }
-    return make_float4(T0, Ti, T1, T2);
-}
-
+// warp-uniform constants; a warp reduction gives the direction's results,
+// which one thread per triangle adds, times omega, to the triangle's float64
+// totals in shared memory after the next barrier.
 __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* __restrict__ rec, int64_t nt,
                                                                  const float4* __restrict__ nd,
                                                                  const double* __restrict__ rad, int n_rad,
@@ -778,8 +671,10 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
                                                                  const AdjPlan p, double* __restrict__ partial)
 {
     __shared__ AdjRad rt[ADJ_RMAX];
-    __shared__ AdjRec wrec[ADJ_TPB / 32][ADJ_RW];      // per warp: its triangles' records for one direction
-    __shared__ double wacc[ADJ_TPB / 32][10][ADJ_RW];  // per warp: its triangles' float64 totals
+    __shared__ float4 sn[ADJ_RMAX];
+    __shared__ AdjRec srec[ADJ_TT];
+    __shared__ double acc[10][ADJ_TT];
+    __shared__ float4 tres[ADJ_TT];  // a direction's results per triangle: (T0, Ti, T1, T2)
     __shared__ TabEntry etab[kTab * kTabRep];
     fill_exp_table(etab);
     const TabEntry* tl = exp_table_lane(etab);
@@ -807,53 +702,149 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
         for (int k = 0; k < 6; ++k) a.pad[k] = 0.0f;
         rt[i] = a;
     }
-    __syncthreads();  // the exponential and radius tables
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    AdjRec* wr = wrec[warp];
-    double (*wa)[ADJ_RW] = wacc[warp];
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
         const int64_t tt = item / p.nchunks;
         const int chunk = (int)(item - tt * p.nchunks);
-        const int64_t tri0 = tt * ADJ_TT + (int64_t)warp * ADJ_RW;  // the warp's first triangle
-        int64_t n_own = nt - tri0;
-        if (n_own > ADJ_RW) n_own = ADJ_RW;
-        if (n_own <= 0) continue;  // warp-uniform: no triangle of this warp in the tile
-        for (int i = lane; i < 10 * ADJ_RW; i += 32) wa[i / ADJ_RW][i % ADJ_RW] = 0.0;
+        const int64_t tri0 = tt * ADJ_TT;
+        __syncthreads();  // the previous item's totals have been written out
+        for (int i = threadIdx.x; i < 10 * ADJ_TT; i += ADJ_TPB) acc[i / ADJ_TT][i % ADJ_TT] = 0.0;
         const int64_t d0 = (int64_t)chunk * p.dirs_per_chunk;
         int64_t d1e = d0 + p.dirs_per_chunk;
         if (d1e > n_dir) d1e = n_dir;
-        for (int64_t d = d0; d < d1e; ++d) {
-            __syncwarp();  // the previous direction is done with the records
-            if (lane < n_own) {
+        for (int64_t d = d0; d <= d1e; ++d) {
+            __syncthreads();
+            // the previous direction's results, times its omega, into the
+            // triangles' float64 totals: one thread per triangle
+            if (d > d0 && threadIdx.x < ADJ_TT && tri0 + threadIdx.x < nt) {
+                const int64_t dp = d - 1;
+                const double ux = dir[dp], uy = dir[n_dir + dp], uz = dir[2 * n_dir + dp];
+                const float4 r = tres[threadIdx.x];
+                const int j = threadIdx.x;
+                acc[0][j] += (double)r.x;
+                acc[1][j] += ux * r.y;
+                acc[2][j] += uy * r.y;
+                acc[3][j] += uz * r.y;
+                acc[4][j] += ux * r.z;
+                acc[5][j] += uy * r.z;
+                acc[6][j] += uz * r.z;
+                acc[7][j] += ux * r.w;
+                acc[8][j] += uy * r.w;
+                acc[9][j] += uz * r.w;
+            }
+            if (d == d1e) break;
+            for (int i = threadIdx.x; i < n_rad; i += ADJ_TPB) sn[i] = nd[d * n_rad + i];
+            if (threadIdx.x < ADJ_TT) {
                 AdjRec r{};
-                adj_dirtri(rec[tri0 + lane], dir, n_dir, d, r.q, r.d1, r.d2);
-                wr[lane] = r;
+                const int64_t tri = tri0 + threadIdx.x;
+                if (tri < nt) adj_dirtri(rec[tri], dir, n_dir, d, r.q, r.d1, r.d2);
+                srec[threadIdx.x] = r;
             }
-            __syncwarp();
-            const double ux = dir[d], uy = dir[n_dir + d], uz = dir[2 * n_dir + d];
-            for (int k = 0; k < n_own; ++k) {
-                const float4 t = adj_dir_tri(tl, wr[k], rt, nd + d * n_rad, n_rad, lane);
-                // the direction's results, times its omega, into the triangle's totals
-                if (lane == 0) {
-                    wa[0][k] += (double)t.x;
-                    wa[1][k] += ux * t.y;
-                    wa[2][k] += uy * t.y;
-                    wa[3][k] += uz * t.y;
-                    wa[4][k] += ux * t.z;
-                    wa[5][k] += uy * t.z;
-                    wa[6][k] += uz * t.z;
-                    wa[7][k] += ux * t.w;
-                    wa[8][k] += uy * t.w;
-                    wa[9][k] += uz * t.w;
+            __syncthreads();
+            for (int j = warp; j < ADJ_TT; j += ADJ_TPB / 32) {
+                if (tri0 + j >= nt) break;  // warp-uniform
+                const AdjDirTri& q = srec[j].q;
+                float S0h = 0.0f, S0t = 0.0f, Sih = 0.0f, Sit = 0.0f, SA = 0.0f, SB = 0.0f;
+                float xP = 0.0f, yP = 0.0f, xQ = 0.0f, yQ = 0.0f, G0 = 0.0f;
+                for (int ir = lane; ir < n_rad; ir += 32) {
+                    const AdjRad a = rt[ir];
+                    const float4 w = sn[ir];
+                    const float rr = w.x, ri = w.y;
+                    const float P = a.rh * q.dmh;
+                    const float e = fmaf(a.rh, q.dmh, -P);
+                    const float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
+                    const float tau = (P - rintf(P)) - w.z;
+                    if (q.gmax0 < a.thr) {
+                        float c, s;
+                        expm_turns(tl, tau, lo, c, s);
+                        const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
+                        const float rho = a.rho, r3 = a.r3;
+                        float sr = fmaf(fmaf(fmaf(fmaf(q.R[5], rho, q.R[4]), rho, q.R[3]), rho, q.R[2]), rho, q.R[1]);
+                        sr = fmaf(sr, rho, q.R[0]) * rho;
+                        float si = fmaf(fmaf(fmaf(q.I[4], rho, q.I[3]), rho, q.I[2]), rho, q.I[1]);
+                        si = fmaf(si, rho, q.I[0]) * r3;
+                        S0h += Zr;
+                        S0t = fmaf(Zr, sr, fmaf(-Zi, si, S0t));
+                        Sih = fmaf(Zi, a.rh, Sih);
+                        Sit = fmaf(fmaf(Zr, si, Zi * sr), a.rh, Sit);
+                        float Ap = fmaf(fmaf(fmaf(fmaf(q.a[4], rho, q.a[3]), rho, q.a[2]), rho, q.a[1]), rho, q.a[0]);
+                        Ap = fmaf(Ap, rho, -1.0f / 24.0f);
+                        const float Bp = fmaf(fmaf(fmaf(q.b[3], rho, q.b[2]), rho, q.b[1]), rho, q.b[0]) * r3;
+                        const float Cq = fmaf(fmaf(fmaf(q.c[3], rho, q.c[2]), rho, q.c[1]), rho, q.c[0]) * r3;
+                        float Eq = fmaf(fmaf(fmaf(q.e[3], rho, q.e[2]), rho, q.e[1]), rho, q.e[0]);
+                        Eq = fmaf(Eq, rho, 1.0f / 120.0f);
+                        SA = fmaf(rho, fmaf(Zr, Ap, -Zi * Bp), SA);
+                        SB = fmaf(r3, fmaf(Zr, Cq, -Zi * Eq), SB);
+                    } else {
+                        float cP, sP, cQ, sQ;
+                        expm_turns(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
+                        expm_turns(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
+                        float scP, dscP, scQ, dscQ;
+                        sincd32(a.rh * q.hP0, scP, dscP);
+                        sincd32(a.rh * q.hQ0, scQ, dscQ);
+                        // X = E sinc(h), Y = i E sinc'(h); x = Re(conj r' X), y = Re(conj r' Y)
+                        const float XPr = cP * scP, XPi = sP * scP, XQr = cQ * scQ, XQi = sQ * scQ;
+                        xP = fmaf(rr, XPr, fmaf(ri, XPi, xP));
+                        xQ = fmaf(rr, XQr, fmaf(ri, XQi, xQ));
+                        yP = fmaf(dscP, fmaf(ri, cP, -rr * sP), yP);
+                        yQ = fmaf(dscQ, fmaf(ri, cQ, -rr * sQ), yQ);
+                        // Re(conj r' i (X_P - X_Q)) / r
+                        G0 = fmaf(fmaf(ri, XPr - XQr, -rr * (XPi - XQi)), a.rinv, G0);
+                    }
                 }
+                // this lane's share of sum_r rho_0, sum_r rho_i r, sum_r rho_1 r, sum_r rho_2 r
+                const float g1d = srec[j].d1, g2d = srec[j].d2;
+                const float ya = -(g1d + g2d) * (1.0f / 3.0f);
+                const float yb = (2.0f * g1d - g2d) * (1.0f / 3.0f);
+                const float yc = (2.0f * g2d - g1d) * (1.0f / 3.0f);
+                const float dq1 = (-yb * yc + 2.0f * ya * yc - ya * yb) * (1.0f / 3.0f);
+                const float dq2 = (-yb * yc - ya * yc + 2.0f * ya * yb) * (1.0f / 3.0f);
+                float T0 = fmaf(0.5f, S0h, S0t);
+                float Ti = fmaf(0.5f, Sih, Sit) * (1.0f / 3.0f);
+                float T1 = fmaf(yb, SA, dq1 * SB);
+                float T2 = fmaf(yc, SA, dq2 * SB);
+                if (q.gmax0 > 0.0f) {  // warp-uniform; with gmax0 = 0 no radius takes the largest-gap branch
+                    const float g3d = g2d - g1d;
+                    const float a1 = fabsf(g1d), a2 = fabsf(g2d), a3 = fabsf(g3d);
+                    const bool caseA = (a2 >= a1) && (a2 >= a3);
+                    const bool caseB = !caseA && (a1 >= a3);
+                    float oP1, oP2, hP1, hP2, oQ1, oQ2, hQ1, hQ2, D0, D1, D2;
+                    if (caseA) {
+                        oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
+                        oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
+                        D0 = g2d; D1 = 0.0f; D2 = 1.0f;
+                    } else if (caseB) {
+                        oP1 = 1.0f / 6; oP2 = 1.0f / 6; hP1 = -0.5f; hP2 = 0.5f;
+                        oQ1 = -1.0f / 3; oQ2 = 1.0f / 6; hQ1 = 0.0f; hQ2 = 0.5f;
+                        D0 = g1d; D1 = 1.0f; D2 = 0.0f;
+                    } else {
+                        oP1 = -1.0f / 3; oP2 = 1.0f / 6; hP1 = 0.0f; hP2 = 0.5f;
+                        oQ1 = 1.0f / 6; oQ2 = -1.0f / 3; hQ1 = 0.5f; hQ2 = 0.0f;
+                        D0 = g3d; D1 = -1.0f; D2 = 1.0f;
+                    }
+                    const float iD = 1.0f / D0;
+                    const float G0D = G0 * iD;
+                    T0 += G0D;
+                    Ti = fmaf(xP - xQ, iD * (1.0f / 3.0f), Ti);
+                    T1 += fmaf(oP1 * xP + hP1 * yP - oQ1 * xQ - hQ1 * yQ, iD, -D1 * G0D * iD);
+                    T2 += fmaf(oP2 * xP + hP2 * yP - oQ2 * xQ - hQ2 * yQ, iD, -D2 * G0D * iD);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    T0 += __shfl_xor_sync(0xffffffffu, T0, o);
+                    Ti += __shfl_xor_sync(0xffffffffu, Ti, o);
+                    T1 += __shfl_xor_sync(0xffffffffu, T1, o);
+                    T2 += __shfl_xor_sync(0xffffffffu, T2, o);
+                }
+                if (lane == 0) tres[j] = make_float4(T0, Ti, T1, T2);
             }
         }
-        __syncwarp();
-        for (int i = lane; i < 10 * ADJ_RW; i += 32) {
-            const int k = i / 10, c = i % 10;
-            if (k < n_own) partial[((int64_t)chunk * nt + tri0 + k) * 10 + c] = wa[c][k];
+        __syncthreads();
+        for (int i = threadIdx.x; i < 10 * ADJ_TT; i += ADJ_TPB) {
+            const int j = i / 10, c = i % 10;
+            const int64_t tri = tri0 + j;
+            if (tri < nt) partial[((int64_t)chunk * nt + tri) * 10 + c] = acc[c][j];
         }
-        __syncwarp();
     }
 }
 
