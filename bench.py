@@ -259,8 +259,9 @@ def cpu_baseline(R, queries, seconds):
     xi, w = oracle.ball_rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
     v, t, s = queries[0]
     threads = oracle.default_threads()
-    # calibrate on growing probes, then size the sample to about `seconds`
-    m = 64
+    # calibrate on growing probes (from 4 nodes: a node of the large mesh is
+    # 327,680 long-double pairs), then size the sample to about `seconds`
+    m = 4
     while True:
         idx = np.arange(0, len(xi), max(1, len(xi) // m))[:m]
         t0 = time.perf_counter()

@@ -59,6 +59,31 @@ __device__ __forceinline__ float sinc32(float x)
     return P * qf;
 }
 
+// sin(x)/x given invx = 1/x (anything where x = 0): sinc32 with the multiple
+// k of pi found by a magic-number add (1.5 * 2^23 is even, so the low bit of
+// the sum is the parity of k, which sets the sign of sin(x) = (-1)^k sin(r))
+// and a multiplication by invx in place of the division.
+__device__ __forceinline__ float sinc32_inv(float x, float invx)
+{
+    const float km = fmaf(x, 0.318309886183790672f, 12582912.0f);
+    const float k = km - 12582912.0f;  // exact
+    float r = fmaf(-k, 3.14159274101257324f, x);
+    r = fmaf(-k, -8.74227766e-8f, r);
+    const float r2 = r * r;
+    float P = -1.0f / 1307674368000.0f;
+    P = fmaf(P, r2, 1.0f / 6227020800.0f);
+    P = fmaf(P, r2, -1.0f / 39916800.0f);
+    P = fmaf(P, r2, 1.0f / 362880.0f);
+    P = fmaf(P, r2, -1.0f / 5040.0f);
+    P = fmaf(P, r2, 1.0f / 120.0f);
+    P = fmaf(P, r2, -1.0f / 6.0f);
+    P = fmaf(P, r2, 1.0f);
+    // for k = 0, r == x exactly and sinc = P
+    const float rs = __int_as_float(__float_as_int(r) ^ (__float_as_int(km) << 31));
+    const float qf = (k == 0.0f) ? 1.0f : rs * invx;
+    return P * qf;
+}
+
 // exp(-i 2 pi tau) for a phase in turns given as the unevaluated float pair
 // tau + tlo, without rounding 2 pi into the argument. tau = j/128 + u with j
 // the nearest multiple (found with a magic-number add, so no float-to-int

@@ -26,9 +26,11 @@
 // rule) and reduces (the quadrature of Eq. (sobolev_2)).
 //
 // Kernels: pair_kernel (one node per thread; float64 path, and the mixed path
-// for explicit node lists and lattice rules), pair_kernel_radial (mixed path,
-// ball rules: per-(direction, triangle) records, radius per thread) and
-// serve_kernel (the serving loop's batched items, either form).
+// for explicit node lists), pair_kernel_precise (the mixed per-node form's
+// extended-precision blocks), pair_kernel_lattice (mixed path, the paper's
+// lattice rule: per-(line, triangle) records), pair_kernel_radial (mixed path,
+// ball rules: per-(direction, triangle) records, radius per thread) and the
+// serving loop's batched kernels, which run the same item bodies.
 #include <cstdint>
 #include <type_traits>
 
@@ -1029,6 +1031,12 @@ __device__ __forceinline__ void lattice_item(const PairArgs& a, const PairPlan& 
     int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
     if (t1 > a.T) t1 = a.T;
     const TriRecF* tris = static_cast<const TriRecF*>(a.tris);
+    // one compensated float32 sum per node over the item, converted once; the
+    // per-node kernel's per-tile phase shift is not needed here: the line
+    // dither varies along the line and the nodes that carry D at a steep
+    // weight are in the extended-precision blocks (mixed vs float64 within
+    // 3e-8 on the paper's ladder either way)
+    Kahan kr, ki;
     for (int64_t tb = t0; tb < t1; tb += LAT_TILE) {
         const int cnt = (int)((t1 - tb) < LAT_TILE ? (t1 - tb) : LAT_TILE);
         const int cnt4 = (cnt + 3) & ~3;
@@ -1057,9 +1065,7 @@ __device__ __forceinline__ void lattice_item(const PairArgs& a, const PairPlan& 
             for (int part = 0; part < LAT_TILE / 32; ++part) gu = max(gu, sm.gmax[s * (LAT_TILE / 32) + part]);
         const float gap_row = __uint_as_float(gu);
         // the node's per-tile phase shift in whole table steps, undone in float64
-        const int shift = tile_shift(node, tb / LAT_TILE);
-        const float magic = kMagic + (float)shift;
-        Kahan kr, ki;
+        const float magic = kMagic;
         const LatRec* rec = sm.rec[slot];
         if (gap_row < kDeltaTiny32)
             lattice_row<2>(tl, rec, cnt4, fi, magic, kr, ki);
@@ -1067,8 +1073,9 @@ __device__ __forceinline__ void lattice_item(const PairArgs& a, const PairPlan& 
             lattice_row<1>(tl, rec, cnt4, fi, magic, kr, ki);
         else
             lattice_row<0>(tl, rec, cnt4, fi, magic, kr, ki);
-        unshift_add(sm.etab, shift, kr.value(), ki.value(), acc_r, acc_i);
     }
+    acc_r = kr.value();
+    acc_i = ki.value();
     const PartialSlots ps{a.partial, a.n};
     node_epilogue<true, MODE, 1>(a, p, nb, chunk, &node, &active, &dith, &acc_r, &acc_i, red, s_last, ps, &node);
 }
@@ -1115,12 +1122,12 @@ struct __align__(16) RadRec {
     float R5, R6, I4;    // the h_10, h_12 and h_11 terms, times gamma
     float gmax0;         // largest |gap| per unit radius
     // divided-difference branch, per unit radius: phase offsets of the two
-    // first differences about the centroid (turns), their half gaps, and
-    // 2 / (largest gap); the case (which vertex pair has the largest gap)
-    // does not depend on r
+    // first differences about the centroid (turns), their half gaps, 2 /
+    // (largest gap) and the half gaps' reciprocals (0 for a zero half gap);
+    // the case (which vertex pair has the largest gap) does not depend on r
     float oP, oQ, hP, hQ;
-    float iD2;
-    float pad[3];
+    float iD2, ihP, ihQ;
+    float pad;
 };
 static_assert(sizeof(RadRec) == 96, "RadRec layout");
 
@@ -1196,7 +1203,9 @@ __device__ __forceinline__ void make_radrec(const TriRecF& t, const float* __res
     o.hQ = caseB ? 0.5f * d2 : 0.5f * d1;
     const float D0 = caseA ? d2 : (caseB ? d1 : d3);
     o.iD2 = D0 != 0.0f ? 2.0f / D0 : 0.0f;  // gmax0 = 0 never takes this branch
-    o.pad[0] = o.pad[1] = o.pad[2] = 0.0f;
+    o.ihP = o.hP != 0.0f ? 1.0f / o.hP : 0.0f;
+    o.ihQ = o.hQ != 0.0f ? 1.0f / o.hQ : 0.0f;
+    o.pad = 0.0f;
 }
 
 // Divided-difference branch of the radial kernel: the per-node version
@@ -1206,9 +1215,9 @@ __device__ __forceinline__ void radial_divdiff(const TabEntry* __restrict__ tl, 
                                                float rinv, const RadRec& t, float& fr, float& fi, float magic)
 {
     float cP, sP, cQ, sQ;  // exp(-i theta) = (c, s)
-    expm_turns(tl, fmaf(r, t.oP, tau), tlo, cP, sP, magic);
-    expm_turns(tl, fmaf(r, t.oQ, tau), tlo, cQ, sQ, magic);
-    const float scP = sinc32(r * t.hP), scQ = sinc32(r * t.hQ);
+    expm_turns_fast(tl, fmaf(r, t.oP, tau), tlo, cP, sP, magic);
+    expm_turns_fast(tl, fmaf(r, t.oQ, tau), tlo, cQ, sQ, magic);
+    const float scP = sinc32_inv(r * t.hP, rinv * t.ihP), scQ = sinc32_inv(r * t.hQ, rinv * t.ihQ);
     // 2 G = i (S_P - S_Q) (2 / D)
     const float dr = cP * scP - cQ * scQ;
     const float di = sP * scP - sQ * scQ;
