@@ -306,6 +306,53 @@ __device__ __forceinline__ void sincd32(float h, float& sc, float& dsc)
     dsc = (sgn * cr - sc) * inv;
 }
 
+// sincd32 given invh = 1/h (anything where h = 0): the reduction by the
+// nearest multiple of pi with a magic-number add (1.5 * 2^23 is even, so the
+// low bit of the sum is the parity of k) and multiplications by invh in place
+// of the division
+__device__ __forceinline__ void sincd32_inv(float h, float invh, float& sc, float& dsc)
+{
+    const float h2 = h * h;
+    if (fabsf(h) < 1.0f) {
+        float a = fmaf(h2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+        a = fmaf(a, h2, 1.0f / 362880.0f);
+        a = fmaf(a, h2, -1.0f / 5040.0f);
+        a = fmaf(a, h2, 1.0f / 120.0f);
+        a = fmaf(a, h2, -1.0f / 6.0f);
+        sc = fmaf(a, h2, 1.0f);
+        float b = fmaf(h2, 1.0f / 518918400.0f, -1.0f / 3991680.0f);
+        b = fmaf(b, h2, 1.0f / 45360.0f);
+        b = fmaf(b, h2, -1.0f / 840.0f);
+        b = fmaf(b, h2, 1.0f / 30.0f);
+        b = fmaf(b, h2, -1.0f / 3.0f);
+        dsc = b * h;
+        return;
+    }
+    const float km = fmaf(h, 0.318309886183790672f, 12582912.0f);
+    const float k = km - 12582912.0f;  // exact
+    float r = fmaf(-k, 3.14159274101257324f, h);
+    r = fmaf(-k, -8.74227766e-8f, r);
+    const float r2 = r * r;
+    float sp = fmaf(r2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+    sp = fmaf(sp, r2, 1.0f / 362880.0f);
+    sp = fmaf(sp, r2, -1.0f / 5040.0f);
+    sp = fmaf(sp, r2, 1.0f / 120.0f);
+    sp = fmaf(sp, r2, -1.0f / 6.0f);
+    const float sr = fmaf(r * r2, sp, r);
+    float cp = fmaf(r2, -1.0f / 87178291200.0f, 1.0f / 479001600.0f);
+    cp = fmaf(cp, r2, -1.0f / 3628800.0f);
+    cp = fmaf(cp, r2, 1.0f / 40320.0f);
+    cp = fmaf(cp, r2, -1.0f / 720.0f);
+    cp = fmaf(cp, r2, 1.0f / 24.0f);
+    cp = fmaf(cp, r2, -0.5f);
+    const float cr = fmaf(cp, r2, 1.0f);
+    // (-1)^k sin r and (-1)^k cos r: the parity of k in the sign bits
+    const int odd = __float_as_int(km) << 31;
+    const float ssr = __int_as_float(__float_as_int(sr) ^ odd), scr = __int_as_float(__float_as_int(cr) ^ odd);
+    sc = ssr * invh;
+    dsc = (scr - sc) * invh;
+}
+
 __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_mixed(const double* __restrict__ xi, int64_t n,
                                                                 const double* __restrict__ resid,
                                                                 const TriRecF* __restrict__ rec, int64_t nt,
@@ -652,8 +699,9 @@ __device__ __forceinline__ void adj_dirtri(const TriRecF& t, const float* __rest
 // Per-(direction, triangle) record of the radial adjoint in shared memory.
 struct __align__(16) AdjRec {
     AdjDirTri q;
-    float d1, d2;  // omega.e1, omega.e2 (the largest-gap case and the Psi_1/Psi_2 factors)
-    float pad[3];
+    float d1, d2;    // omega.e1, omega.e2 (the largest-gap case and the Psi_1/Psi_2 factors)
+    float ihP, ihQ;  // 1 / hP0, 1 / hQ0 (0 where the half gap is 0)
+    float pad;
 };
 static_assert(sizeof(AdjRec) % 16 == 0, "AdjRec layout");
 
@@ -737,7 +785,11 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
             if (threadIdx.x < ADJ_TT) {
                 AdjRec r{};
                 const int64_t tri = tri0 + threadIdx.x;
-                if (tri < nt) adj_dirtri(rec[tri], dir, n_dir, d, r.q, r.d1, r.d2);
+                if (tri < nt) {
+                    adj_dirtri(rec[tri], dir, n_dir, d, r.q, r.d1, r.d2);
+                    r.ihP = r.q.hP0 != 0.0f ? 1.0f / r.q.hP0 : 0.0f;
+                    r.ihQ = r.q.hQ0 != 0.0f ? 1.0f / r.q.hQ0 : 0.0f;
+                }
                 srec[threadIdx.x] = r;
             }
             __syncthreads();
@@ -756,7 +808,7 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
                     const float tau = (P - rintf(P)) - w.z;
                     if (q.gmax0 < a.thr) {
                         float c, s;
-                        expm_turns(tl, tau, lo, c, s);
+                        expm_turns_fast(tl, tau, lo, c, s);
                         const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
                         const float rho = a.rho, r3 = a.r3;
                         float sr = fmaf(fmaf(fmaf(fmaf(q.R[5], rho, q.R[4]), rho, q.R[3]), rho, q.R[2]), rho, q.R[1]);
@@ -777,11 +829,11 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
                         SB = fmaf(r3, fmaf(Zr, Cq, -Zi * Eq), SB);
                     } else {
                         float cP, sP, cQ, sQ;
-                        expm_turns(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
-                        expm_turns(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
+                        expm_turns_fast(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
+                        expm_turns_fast(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
                         float scP, dscP, scQ, dscQ;
-                        sincd32(a.rh * q.hP0, scP, dscP);
-                        sincd32(a.rh * q.hQ0, scQ, dscQ);
+                        sincd32_inv(a.rh * q.hP0, a.rinv * srec[j].ihP, scP, dscP);
+                        sincd32_inv(a.rh * q.hQ0, a.rinv * srec[j].ihQ, scQ, dscQ);
                         // X = E sinc(h), Y = i E sinc'(h); x = Re(conj r' X), y = Re(conj r' Y)
                         const float XPr = cP * scP, XPi = sP * scP, XQr = cQ * scQ, XQi = sQ * scQ;
                         xP = fmaf(rr, XPr, fmaf(ri, XPi, xP));

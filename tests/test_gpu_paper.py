@@ -162,3 +162,20 @@ def test_lattice_kernel_distance_matches_oracle(ctx, N, s):
     rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
     dmx = ctx.distance(rule, v, t, None, s, wd.WD_MIXED)
     assert dmx == pytest.approx(d_or, rel=1e-7), (dmx - d_or) / d_or
+
+
+def test_lattice_kernel_full_lattice_and_mesh_reference(ctx):
+    """The lattice-line form on a non-Hermitian M = 128 rule (full lines only)
+    and with a second mesh as the reference measure (its triangles enter with
+    negated gamma), against the oracle."""
+    v, t = synth.icosphere_recursive(1)
+    xo, wo = oracle.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, False)
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, False)
+    d_or = oracle.distance(xo, wo, 3.0, v, t, wscale=oracle.PAPER_WSCALE)
+    assert ctx.distance(rule, v, t, None, 3.0, wd.WD_MIXED) == pytest.approx(d_or, rel=1e-7)
+    v0, t0 = synth.icosphere_recursive(0)
+    xo, wo = oracle.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    nu = ("mesh", v0, t0)
+    d_or = oracle.distance(xo, wo, 3.0, v, t, nu=nu, wscale=oracle.PAPER_WSCALE)
+    assert ctx.distance(rule, v, t, nu, 3.0, wd.WD_MIXED) == pytest.approx(d_or, rel=1e-7)

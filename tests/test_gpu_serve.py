@@ -171,3 +171,21 @@ def test_lattice_rule_queries(ctx, prec):
     finally:
         wd.wd_serve_stop(sv)
     assert served == alone
+
+
+def test_paper_lattice_rule_queries(ctx):
+    """The paper's M = 128 lattice in the server: its lattice-line form and
+    extended-precision blocks give wd_distance's bits, alone and in the mix."""
+    rules = [(synth.PAPER_XI_MAX, synth.PAPER_M, 0, 0, True, wd.WD_RULE_CUBE_TRAP)]
+    cube = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+    qs = [(synth.icosphere_recursive(k)[0], synth.icosphere_recursive(k)[1], s) for k, s in ((1, 10.0), (3, 10.0),
+                                                                                            (2, 3.0))]
+    alone = [ctx.distance(cube, v, t, None, s, wd.WD_MIXED) for (v, t, s) in qs]
+    sv = wd.wd_serve_start(ctx.handle, rules, precision=wd.WD_MIXED, max_slots=4, pairs_per_launch=200_000_000)
+    try:
+        tickets = [wd.wd_serve_submit(sv, v, t, s, synth.PAPER_XI_MAX) for (v, t, s) in qs]
+        served = [wd.wd_serve_wait(sv, tk, 600000) for tk in tickets]
+        st = wd.wd_serve_stats(sv)
+    finally:
+        wd.wd_serve_stop(sv)
+    assert served == alone and st["launches"] >= 2
