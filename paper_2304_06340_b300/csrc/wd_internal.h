@@ -239,7 +239,7 @@ constexpr int WD_NPB = 256;   // nodes per block: one node per thread
 constexpr int WD_TILE = 128;  // triangles per shared-memory tile
 // radial plan (ball rules, mixed path): a block covers WD_RAD_ND directions x
 // WD_RAD_NR radii; each thread takes WD_RAD_RPT radii of one direction
-constexpr int WD_RAD_RPT = 1;  // radii per thread; 2 ran slower (381 vs 407 Gpair/s on the n=64 sweep query)
+constexpr int WD_RAD_RPT = 1;  // radii per thread; 2 (3 blocks per SM) ran 7 % faster on all-Taylor rows but 25 % slower where rows mix branches
 constexpr int WD_RAD_NR = 64;                        // radii per block
 constexpr int WD_RAD_TPD = WD_RAD_NR / WD_RAD_RPT;   // threads per direction
 constexpr int WD_RAD_ND = WD_NPB / WD_RAD_TPD;       // directions per block

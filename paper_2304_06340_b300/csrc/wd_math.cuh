@@ -36,6 +36,23 @@ __device__ __forceinline__ float node_dither(int64_t node)
     return (float)(h >> 12) * 9.5367431640625e-7f - 0.5f;  // 20 bits, exact in float32
 }
 
+// The same hash as a whole number of exp-table steps, j in [-kTab/2, kTab/2)
+// (kTab = 128 steps per turn), for a kernel that feeds its unreduced phase
+// tau straight to the table exponential with the magic constant kMagic - j:
+// the table index moves by -j while the residual u stays exact, so every pair
+// of the node comes out multiplied by exp(2 pi i j / kTab), undone in float64
+// as the dither d = j / kTab. No rounding enters the phase itself.
+__device__ __forceinline__ int node_dither_steps(int64_t node)
+{
+    uint32_t h = (uint32_t)node * 0x9E3779B9u + 0x7F4A7C15u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (int)(h >> 25) - 64;
+}
+
 // sin(x)/x: reduction by the nearest multiple of pi (two-constant split) and
 // the Taylor polynomial of sin(r)/r on |r| <= pi/2 (remainder < 5e-10).
 __device__ __forceinline__ float sinc32(float x)
@@ -160,12 +177,20 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, floa
     ei = -s;
 }
 
-// expm_turns with the residual angle x = 2 pi (u + tlo) formed as one float
-// (u times the float 2 pi, plus 2 pi tlo) instead of a float pair: 3
-// instructions fewer. |x| <= pi/128, so the rounding of x is below 1.5e-9 rad
-// and the float 2 pi scales x by 1 - 2.8e-8, a phase error odd in u and so of
-// zero mean over the dithered phases; both are far below the 6e-8 rounding
-// of the result. The dropped x_lo^2 and x_lo x^3 terms are below 1e-15.
+// expm_turns with a shorter residual: v = u + tlo stays in turns (one add),
+// and cos(2 pi v) - 1 and sin(2 pi v) are polynomials in v with the powers of
+// 2 pi folded into their coefficients, sin(2 pi v) as one float instead of a
+// float pair: one instruction fewer than the residual in radians.
+// The leading coefficients (2 pi)^2 / 2 and 2 pi are float pairs whose high
+// products enter each final FMA exactly. Rounded alone they would scale
+// every residual sine by 1 + 2.8e-8 and every cos - 1 by 1 - 2.9e-8; a kernel
+// whose residual v is not dithered (see node_dither_steps) sees those as a
+// coherent frequency-scale error and a coherent real scale error of ~3e-12 at
+// low frequency, which move D against mu^ - nu^ there (measured: twice the
+// random spread of D on a low-frequency shell window for the cosine alone).
+// |v| <= 1/256 + |tlo|: the rounding of v is below 2.5e-10 turns, that of
+// sin(2 pi v) below 1.5e-9, and the dropped v^5 (sine) and v^6 (cosine)
+// terms below 7.5e-11, all far below the 6e-8 rounding of the result.
 __device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl, float tau, float tlo, float& er,
                                                 float& ei, float magic = kMagic)
 {
@@ -173,13 +198,15 @@ __device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl,
     const int idx = __float_as_int(km) & (kTab - 1);
     const float k = km - magic;                   // exact
     const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/256
-    const float x = fmaf(u, 6.28318548202514648f, tlo * 6.28318548202514648f);
-    const float x2 = x * x;
-    const float dc = x2 * fmaf(x2, 1.0f / 24.0f, -0.5f);  // cos x - 1
-    const float ds = (x * x2) * (-1.0f / 6.0f);           // sin x - x
+    const float v = u + tlo;
+    const float v2 = v * v;
+    // cos 2 pi v - 1 = -(2 pi)^2 v^2 / 2 + (2 pi)^4 v^4 / 24 and
+    // sin 2 pi v = 2 pi v - (2 pi)^3 v^3 / 6, the leading constants split
+    const float dc = fmaf(v2, -19.7392082214355469f, v2 * fmaf(v2, 64.9393940226682914f, -5.80743176215037e-07f));
+    const float sx = fmaf(v, 6.28318548202514648f, v * fmaf(v2, -41.3417022403997534f, -1.74845553146951715e-07f));
     const TabEntry t = tl[idx * kTabRep];
-    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, x, fmaf(-t.sh, ds, t.cl)));
-    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, x, fmaf(t.ch, ds, t.sl)));
+    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, sx, t.cl));
+    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, sx, t.sl));
     er = c;
     ei = -s;
 }

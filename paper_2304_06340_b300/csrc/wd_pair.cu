@@ -1260,7 +1260,7 @@ struct RadThread {
     float rho[WD_RAD_RPT], r3[WD_RAD_RPT];   // r^2, r^3
     float thr[WD_RAD_RPT];                   // Taylor branch while gmax0 < thr = DELTA / r
     float rinv[WD_RAD_RPT];                  // 1 / r
-    float dith[WD_RAD_RPT];                  // the node's phase dither
+    float mg[WD_RAD_RPT];                    // kMagic - j: the node's dither of j table steps
 };
 
 // dith_base: index, in the full rule, of the first node of a radial window
@@ -1287,7 +1287,7 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
         h.r3[q] = (float)(r * r * r);
         h.thr[q] = h.active[q] ? (float)((double)kDelta32 / r) : 3.402823466e38f;
         h.rinv[q] = h.active[q] ? (float)(1.0 / r) : 0.0f;
-        h.dith[q] = node_dither(dith_base + h.node[q]);
+        h.mg[q] = kMagic - (float)node_dither_steps(dith_base + h.node[q]);  // exact
         // A warp holds 32 consecutive radii of one direction, and the branch
         // test r gmax0 < DELTA splits it wherever a record's seam falls inside
         // its radius range; the split warp then runs both branches. Where the
@@ -1305,14 +1305,17 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
     return h;
 }
 
-// Dithered centroid phase in turns of record t at the thread's q-th radius:
-// (rh + rlo)(dmh + dml) reduced mod 1, as the pair (tau, lo)
-__device__ __forceinline__ void radial_phase(const RadRec& t, const RadThread& h, int q, float& tau, float& lo)
+// Centroid phase in turns of record t at the thread's q-th radius,
+// (rh + rlo)(dmh + dml) as the pair (P, lo): P the rounded high product, lo
+// its exact rounding error plus the low products. P is not reduced mod 1:
+// the table exponential takes it whole (|P| <= 2^15 keeps 128 P below the
+// magic constant's integer range) and leaves u = P - k/128 exact, and the
+// node's dither enters as table steps in h.mg, so no rounding enters here.
+__device__ __forceinline__ void radial_phase(const RadRec& t, const RadThread& h, int q, float& P, float& lo)
 {
-    const float P = h.rh[q] * t.dmh;
+    P = h.rh[q] * t.dmh;
     const float e = fmaf(h.rh[q], t.dmh, -P);
     lo = fmaf(h.rh[q], t.dml, fmaf(h.rlo[q], t.dmh, e));
-    tau = (P - rintf(P)) - h.dith[q];
 }
 
 // Taylor branch of record t at the thread's q-th radius: the tail as a
@@ -1336,22 +1339,27 @@ __device__ __forceinline__ void radial_taylor(const TabEntry* __restrict__ tl, c
 }
 
 // F_T of record t at the thread's q-th radius (dithered phase, Taylor branch
-// as a polynomial in r^2 or the largest-gap branch)
+// as a polynomial in r^2 or the largest-gap branch); REDUCE takes the phase
+// mod 1 first (exact), for rows whose phases may reach the table
+// exponential's range limit
+template <bool REDUCE>
 __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
                                             int q, float& fr, float& fi, float magic)
 {
-    float tau, lo;
-    radial_phase(t, h, q, tau, lo);
+    float P, lo;
+    radial_phase(t, h, q, P, lo);
+    if (REDUCE) P -= rintf(P);
     if (t.gmax0 < h.thr[q])
-        radial_taylor<false>(tl, t, h, q, tau, lo, fr, fi, magic);
-    else
-        radial_divdiff(tl, tau, lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
+        radial_taylor<false>(tl, t, h, q, P, lo, fr, fi, magic);
+    else  // the offsets r oP, r oQ are added to the exactly reduced phase
+        radial_divdiff(tl, P - rintf(P), lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
 }
 
 // One tile row of records at the thread's radii, in groups of 8 pairs
 // (float32 sums, dithered phases: random roundings), Kahan across groups.
 // VAR 0: per-pair branch choice; 1: every pair in the Taylor branch; 2: every
-// pair in the Taylor branch with all gaps below DELTA_S (short series).
+// pair in the Taylor branch with all gaps below DELTA_S (short series); 3: as
+// 0 with the phase reduced mod 1 first (phases of 2^13 turns or more).
 template <int VAR>
 __device__ __forceinline__ void radial_row(const TabEntry* __restrict__ tl, const RadRec* __restrict__ rec, int cnt8,
                                            const RadThread& h, Kahan* kr, Kahan* ki)
@@ -1366,12 +1374,12 @@ __device__ __forceinline__ void radial_row(const TabEntry* __restrict__ tl, cons
 #pragma unroll
             for (int q = 0; q < WD_RAD_RPT; ++q) {
                 float fr, fi;
-                if (VAR == 0) {
-                    radial_pair(tl, t, h, q, fr, fi, kMagic);
+                if (VAR == 0 || VAR == 3) {
+                    radial_pair<VAR == 3>(tl, t, h, q, fr, fi, h.mg[q]);
                 } else {
-                    float tau, lo;
-                    radial_phase(t, h, q, tau, lo);
-                    radial_taylor<VAR == 2>(tl, t, h, q, tau, lo, fr, fi, kMagic);
+                    float P, lo;
+                    radial_phase(t, h, q, P, lo);
+                    radial_taylor<VAR == 2>(tl, t, h, q, P, lo, fr, fi, h.mg[q]);
                 }
                 br[q] += fr;
                 bi[q] += fi;
@@ -1397,6 +1405,7 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
     static_assert(WD_RAD_TILE % 32 == 0 && WD_NPB % 32 == 0, "a warp builds records of one direction");
     constexpr int kParts = WD_RAD_TILE / 32;                  // warps' worth of records per direction row
     __shared__ unsigned int s_gmax[WD_RAD_ND * kParts];       // largest gmax0 per 32 records, as bits
+    __shared__ unsigned int s_pmax[WD_RAD_ND * kParts];       // largest |dmh| per 32 records, as bits
     __shared__ float s_rmax[WD_NPB / 32];                     // largest active radius per warp
     {
         float rm = 0.0f;
@@ -1420,7 +1429,7 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
         for (int i = threadIdx.x; i < WD_RAD_ND * WD_RAD_TILE; i += WD_NPB) {
             const int di = i / WD_RAD_TILE, j = i % WD_RAD_TILE;
             const int64_t dd = h.dg * WD_RAD_ND + di;
-            float gm = 0.0f;
+            float gm = 0.0f, pm = 0.0f;
             if (j < cnt8) {
                 RadRec o;
                 if (j < cnt && dd < n_dir) {
@@ -1430,10 +1439,15 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
                     o = RadRec{};
                 }
                 gm = o.gmax0;
+                pm = fabsf(o.dmh);
                 tile[di][j] = o;
             }
             const unsigned int wm = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
-            if ((threadIdx.x & 31) == 0) s_gmax[i / 32] = wm;
+            const unsigned int pmx = __reduce_max_sync(0xffffffffu, __float_as_uint(pm));
+            if ((threadIdx.x & 31) == 0) {
+                s_gmax[i / 32] = wm;
+                s_pmax[i / 32] = pmx;
+            }
         }
         __syncthreads();
         bool any_node = false;
@@ -1448,11 +1462,19 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
         // every lane of the warp in the Taylor branch, the row runs without
         // the per-pair branch test, and with the short series where every
         // gap is below DELTA_S; the choice is the same for the whole warp.
-        unsigned int gu = 0u;
+        unsigned int gu = 0u, pu = 0u;
 #pragma unroll
-        for (int p = 0; p < kParts; ++p) gu = max(gu, s_gmax[h.dl * kParts + p]);
-        const float gap_row = __uint_as_float(gu) * s_rmax[threadIdx.x >> 5];  // bounds every lane's gaps
-        if (gap_row < kDeltaShort32)
+        for (int p = 0; p < kParts; ++p) {
+            gu = max(gu, s_gmax[h.dl * kParts + p]);
+            pu = max(pu, s_pmax[h.dl * kParts + p]);
+        }
+        const float rmax = s_rmax[threadIdx.x >> 5];
+        const float gap_row = __uint_as_float(gu) * rmax;  // bounds every lane's gaps
+        // the table exponential takes the unreduced phase while |128 P| stays
+        // well inside the magic constant's 2^22 integer range
+        if (__uint_as_float(pu) * rmax >= 8192.0f)
+            radial_row<3>(tl, rec, cnt8, h, kr, ki);
+        else if (gap_row < kDeltaShort32)
             radial_row<2>(tl, rec, cnt8, h, kr, ki);
         else if (gap_row < kDelta32)
             radial_row<1>(tl, rec, cnt8, h, kr, ki);
@@ -1485,8 +1507,11 @@ __device__ __forceinline__ void radial_item(const PairArgs& a, const PairPlan& p
     if (t1 > a.T) t1 = a.T;
     double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
     radial_sum(sm.tile, sm.etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
+    float dith[WD_RAD_RPT];  // j / kTab turns, exact
+#pragma unroll
+    for (int q = 0; q < WD_RAD_RPT; ++q) dith[q] = (kMagic - h.mg[q]) * (1.0f / kTab);
     const PartialSlots ps{a.partial, a.n};
-    node_epilogue<true, MODE, WD_RAD_RPT, false>(a, p, nb, chunk, h.node, h.active, h.dith, acc_r, acc_i, red,
+    node_epilogue<true, MODE, WD_RAD_RPT, false>(a, p, nb, chunk, h.node, h.active, dith, acc_r, acc_i, red,
                                                  s_last, ps, h.node);
 }
 
