@@ -191,14 +191,11 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, floa
 // |v| <= 1/256 + |tlo|: the rounding of v is below 2.5e-10 turns, that of
 // sin(2 pi v) below 1.5e-9, and the dropped v^5 (sine) and v^6 (cosine)
 // terms below 7.5e-11, all far below the 6e-8 rounding of the result.
-__device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl, float tau, float tlo, float& er,
-                                                float& ei, float magic = kMagic)
+// The residual part of expm_turns_fast: table entry idx (of the lane's
+// replica) times exp(-2 pi i v), |v| <= 1/256 + a few 2^-24, as (er, ei).
+__device__ __forceinline__ void expm_residual(const TabEntry* __restrict__ tl, int idx, float v, float& er,
+                                              float& ei)
 {
-    const float km = fmaf(tau, (float)kTab, magic);
-    const int idx = __float_as_int(km) & (kTab - 1);
-    const float k = km - magic;                   // exact
-    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/256
-    const float v = u + tlo;
     const float v2 = v * v;
     // cos 2 pi v - 1 = -(2 pi)^2 v^2 / 2 + (2 pi)^4 v^4 / 24 and
     // sin 2 pi v = 2 pi v - (2 pi)^3 v^3 / 6, the leading constants split
@@ -210,6 +207,22 @@ __device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl,
     er = c;
     ei = -s;
 }
+
+__device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl, float tau, float tlo, float& er,
+                                                float& ei, float magic = kMagic)
+{
+    const float km = fmaf(tau, (float)kTab, magic);
+    const int idx = __float_as_int(km) & (kTab - 1);
+    const float k = km - magic;                   // exact
+    const float u = fmaf(-1.0f / kTab, k, tau);   // exact, |u| <= 1/256
+    expm_residual(tl, idx, u + tlo, er, ei);
+}
+
+// kMagic in turns, 1.5 * 2^16: adding it to a phase in turns (|phase| < 2^15)
+// rounds the phase to whole table steps, 2^-7 turns, whose count mod kTab is
+// then the low 7 bits of the sum. kMagicTurns - j / kTab (j an integer,
+// |j| <= kTab / 2) is exact and moves the index by -j the same way.
+constexpr float kMagicTurns = kMagic / kTab;
 
 // Per-(node, triangle tile) phase shift in whole table steps, s in [0, kTab):
 // a second dither that varies across the tiles of one node. At low frequency

@@ -1228,20 +1228,17 @@ __device__ __forceinline__ void radial_divdiff(const TabEntry* __restrict__ tl, 
     fi = fmaf(t.g2, gi, t.l2 * gi);
 }
 
-// Taylor branch end for the radial kernel. With g2 = gamma/2 and
-// l2 = gamma_lo/2 (both exact), the gamma-scaled tail gamma (sr + i si) as
-// (ar - l2) + i ai, i.e. ar = l2 + gamma sr:
+// Taylor branch end for the radial kernel, (c, s) = exp(-i theta). With
+// g2 = gamma/2 and l2 = gamma_lo/2 (both exact), the gamma-scaled tail
+// gamma (sr + i si) as (ar - l2) + i ai, i.e. ar = l2 + gamma sr:
 //     F = gamma (c + i s)(1/2 + sr + i si)
 //       = g2 (c + i s) + (c + i s)(ar + i ai),
 // in one final rounding per component as in taylor_combine. The product
 // gamma_lo * tail (2^-24 of a zero-mean term already below the float32
 // rounding of F) is left out.
-__device__ __forceinline__ void taylor_combine_half(const TabEntry* __restrict__ tl, float tau, float tlo,
-                                                    float ar, float ai, float g2, float& fr, float& fi,
-                                                    float magic)
+__device__ __forceinline__ void taylor_combine_half(float c, float s, float ar, float ai, float g2, float& fr,
+                                                    float& fi)
 {
-    float c, s;
-    expm_turns_fast(tl, tau, tlo, c, s, magic);
     fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
     fi = fmaf(g2, s, fmaf(s, ar, c * ai));
 }
@@ -1260,7 +1257,7 @@ struct RadThread {
     float rho[WD_RAD_RPT], r3[WD_RAD_RPT];   // r^2, r^3
     float thr[WD_RAD_RPT];                   // Taylor branch while gmax0 < thr = DELTA / r
     float rinv[WD_RAD_RPT];                  // 1 / r
-    float mg[WD_RAD_RPT];                    // kMagic - j: the node's dither of j table steps
+    float mt[WD_RAD_RPT];                    // kMagicTurns - j / kTab: the node's dither of j table steps
 };
 
 // dith_base: index, in the full rule, of the first node of a radial window
@@ -1287,7 +1284,7 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
         h.r3[q] = (float)(r * r * r);
         h.thr[q] = h.active[q] ? (float)((double)kDelta32 / r) : 3.402823466e38f;
         h.rinv[q] = h.active[q] ? (float)(1.0 / r) : 0.0f;
-        h.mg[q] = kMagic - (float)node_dither_steps(dith_base + h.node[q]);  // exact
+        h.mt[q] = kMagicTurns - (float)node_dither_steps(dith_base + h.node[q]) * (1.0f / kTab);  // exact
         // A warp holds 32 consecutive radii of one direction, and the branch
         // test r gmax0 < DELTA splits it wherever a record's seam falls inside
         // its radius range; the split warp then runs both branches. Where the
@@ -1307,10 +1304,7 @@ __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ ra
 
 // Centroid phase in turns of record t at the thread's q-th radius,
 // (rh + rlo)(dmh + dml) as the pair (P, lo): P the rounded high product, lo
-// its exact rounding error plus the low products. P is not reduced mod 1:
-// the table exponential takes it whole (|P| <= 2^15 keeps 128 P below the
-// magic constant's integer range) and leaves u = P - k/128 exact, and the
-// node's dither enters as table steps in h.mg, so no rounding enters here.
+// its exact rounding error plus the low products.
 __device__ __forceinline__ void radial_phase(const RadRec& t, const RadThread& h, int q, float& P, float& lo)
 {
     P = h.rh[q] * t.dmh;
@@ -1318,14 +1312,36 @@ __device__ __forceinline__ void radial_phase(const RadRec& t, const RadThread& h
     lo = fmaf(h.rh[q], t.dml, fmaf(h.rlo[q], t.dmh, e));
 }
 
-// Taylor branch of record t at the thread's q-th radius: the tail as a
-// polynomial in rho = r^2, to h_12 or, when every gap is below DELTA_S, to h_9
+// exp(-2 pi i (rh + rlo)(dmh + dml)) exp(2 pi i j / kTab) of record t at the
+// thread's q-th radius, j the node's dither in table steps, with the phase
+// reduction folded into the table lookup: adding mt = kMagicTurns - j / kTab
+// to the exact product rh dmh rounds it to k table steps (|rh dmh| < 2^13,
+// see radial_sum) and leaves the index k - j in the low bits; mt minus that
+// sum is -k / kTab exactly, and one FMA with the exact product again gives
+// the residual rh dmh - k / kTab with a single rounding (below 2.5e-10
+// turns). The low products are summed apart and added once: added one by
+// one to the residual, each would be rounded away wherever it is below half
+// the residual's ulp, i.e. the pair would be evaluated at the float radius
+// rh and the float rate dmh, a coherent error that moved D on low-frequency
+// shells by 8e-8. No rounding of the whole phase enters the pair.
+__device__ __forceinline__ void radial_expm(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
+                                            int q, float& er, float& ei)
+{
+    const float m = fmaf(h.rh[q], t.dmh, h.mt[q]);
+    const int idx = __float_as_int(m) & (kTab - 1);
+    const float nk = h.mt[q] - m;  // exact
+    const float u = fmaf(h.rh[q], t.dmh, nk);
+    const float w = fmaf(h.rh[q], t.dml, h.rlo[q] * t.dmh);
+    expm_residual(tl, idx, u + w, er, ei);
+}
+
+// The gamma-scaled Taylor tail of record t at the thread's q-th radius as a
+// polynomial in rho = r^2 (ar including gamma_lo / 2), to h_12 or, when every
+// gap is below DELTA_S, to h_9
 template <bool SHORT>
-__device__ __forceinline__ void radial_taylor(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
-                                              int q, float tau, float lo, float& fr, float& fi, float magic)
+__device__ __forceinline__ void radial_tail(const RadRec& t, const RadThread& h, int q, float& ar, float& ai)
 {
     const float rho = h.rho[q];
-    float ar, ai;
     if (SHORT) {
         ar = fmaf(fmaf(t.R[3], rho, t.R[2]), rho, t.R[1]);
         ai = fmaf(fmaf(t.I[3], rho, t.I[2]), rho, t.I[1]);
@@ -1335,24 +1351,43 @@ __device__ __forceinline__ void radial_taylor(const TabEntry* __restrict__ tl, c
     }
     ar = fmaf(fmaf(ar, rho, t.R[0]), rho, t.l2);
     ai = fmaf(ai, rho, t.I[0]) * h.r3[q];
-    taylor_combine_half(tl, tau, lo, ar, ai, t.g2, fr, fi, magic);
+}
+
+// Taylor branch of record t at the thread's q-th radius
+template <bool SHORT>
+__device__ __forceinline__ void radial_taylor(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
+                                              int q, float& fr, float& fi)
+{
+    float ar, ai, c, s;
+    radial_tail<SHORT>(t, h, q, ar, ai);
+    radial_expm(tl, t, h, q, c, s);
+    taylor_combine_half(c, s, ar, ai, t.g2, fr, fi);
 }
 
 // F_T of record t at the thread's q-th radius (dithered phase, Taylor branch
 // as a polynomial in r^2 or the largest-gap branch); REDUCE takes the phase
-// mod 1 first (exact), for rows whose phases may reach the table
-// exponential's range limit
+// mod 1 first (exact) in both branches, for rows whose phases reach 2^13
+// turns, beyond radial_expm's range
 template <bool REDUCE>
 __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, const RadRec& t, const RadThread& h,
-                                            int q, float& fr, float& fi, float magic)
+                                            int q, float& fr, float& fi)
 {
+    const float magic = h.mt[q] * (float)kTab;  // kMagic - j, exact
+    if (!REDUCE && t.gmax0 < h.thr[q]) {
+        radial_taylor<false>(tl, t, h, q, fr, fi);
+        return;
+    }
     float P, lo;
     radial_phase(t, h, q, P, lo);
-    if (REDUCE) P -= rintf(P);
-    if (t.gmax0 < h.thr[q])
-        radial_taylor<false>(tl, t, h, q, P, lo, fr, fi, magic);
-    else  // the offsets r oP, r oQ are added to the exactly reduced phase
-        radial_divdiff(tl, P - rintf(P), lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
+    P -= rintf(P);  // exact
+    if (REDUCE && t.gmax0 < h.thr[q]) {
+        float ar, ai, c, s;
+        radial_tail<false>(t, h, q, ar, ai);
+        expm_turns_fast(tl, P, lo, c, s, magic);
+        taylor_combine_half(c, s, ar, ai, t.g2, fr, fi);
+    } else {  // the offsets r oP, r oQ are added to the reduced phase
+        radial_divdiff(tl, P, lo, h.rh[q], h.rinv[q], t, fr, fi, magic);
+    }
 }
 
 // One tile row of records at the thread's radii, in groups of 8 pairs
@@ -1374,13 +1409,10 @@ __device__ __forceinline__ void radial_row(const TabEntry* __restrict__ tl, cons
 #pragma unroll
             for (int q = 0; q < WD_RAD_RPT; ++q) {
                 float fr, fi;
-                if (VAR == 0 || VAR == 3) {
-                    radial_pair<VAR == 3>(tl, t, h, q, fr, fi, h.mg[q]);
-                } else {
-                    float P, lo;
-                    radial_phase(t, h, q, P, lo);
-                    radial_taylor<VAR == 2>(tl, t, h, q, P, lo, fr, fi, h.mg[q]);
-                }
+                if (VAR == 0 || VAR == 3)
+                    radial_pair<VAR == 3>(tl, t, h, q, fr, fi);
+                else
+                    radial_taylor<VAR == 2>(tl, t, h, q, fr, fi);
                 br[q] += fr;
                 bi[q] += fi;
             }
@@ -1509,7 +1541,7 @@ __device__ __forceinline__ void radial_item(const PairArgs& a, const PairPlan& p
     radial_sum(sm.tile, sm.etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
     float dith[WD_RAD_RPT];  // j / kTab turns, exact
 #pragma unroll
-    for (int q = 0; q < WD_RAD_RPT; ++q) dith[q] = (kMagic - h.mg[q]) * (1.0f / kTab);
+    for (int q = 0; q < WD_RAD_RPT; ++q) dith[q] = kMagicTurns - h.mt[q];
     const PartialSlots ps{a.partial, a.n};
     node_epilogue<true, MODE, WD_RAD_RPT, false>(a, p, nb, chunk, h.node, h.active, dith, acc_r, acc_i, red,
                                                  s_last, ps, h.node);
