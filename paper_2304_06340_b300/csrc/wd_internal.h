@@ -141,19 +141,19 @@ struct wd_ctx {
     std::atomic<int64_t> launches{0};
     // resident blocks of each kernel on this context's device (0: not yet
     // queried); written once per slot, any thread may fill a slot
-    std::atomic<int> occupancy[24] = {};  // OccSlot
+    std::atomic<int> occupancy[32] = {};  // OccSlot
 };
 
 // resident-block slots of wd_ctx::occupancy
 enum OccSlot {
     OCC_PAIR = 0,          // + 3 * mixed + mode (6 slots)
-    OCC_RADIAL = 6,        // + mode (3 slots)
-    OCC_SERVE = 9,         // + form, mixed per-node form at + 2 (3 slots)
-    OCC_ADJOINT = 12,      // + 0 float64, 1 mixed, 2 radial (3 slots)
-    OCC_PRECISE = 15,      // + mode (3 slots)
-    OCC_SERVE_PRECISE = 18,
-    OCC_LATTICE = 19,      // + mode (3 slots)
-    OCC_SERVE_LATTICE = 22,
+    OCC_RADIAL = 6,        // + 3 * mode + radius group index (9 slots)
+    OCC_SERVE = 15,        // + form, mixed per-node form at + 2 (3 slots)
+    OCC_ADJOINT = 18,      // + 0 float64, 1 mixed, 2 radial (3 slots)
+    OCC_PRECISE = 21,      // + mode (3 slots)
+    OCC_SERVE_PRECISE = 24,
+    OCC_LATTICE = 25,      // + mode (3 slots)
+    OCC_SERVE_LATTICE = 28,
 };
 // the cached count of slot `slot`, or query(kernel) * SMs stored there
 template <typename K>
@@ -192,6 +192,7 @@ enum PairMode { MODE_DIST = 0, MODE_FT = 1, MODE_RESID = 2 };
 
 struct PairPlan {
     bool radial = false;      // radius x direction node blocks (ball rules, mixed path)
+    int rad_nr = 0;           // radial plan: radii per block (radius group)
     bool lattice = false;     // per-node blocks with lattice-line records (cube rules, mixed path)
     int64_t n_dg = 0;         // radial plan: direction groups
     int n_rg = 0;             // radial plan: radius groups
@@ -237,13 +238,20 @@ struct PairArgs {
 
 constexpr int WD_NPB = 256;   // nodes per block: one node per thread
 constexpr int WD_TILE = 128;  // triangles per shared-memory tile
-// radial plan (ball rules, mixed path): a block covers WD_RAD_ND directions x
-// WD_RAD_NR radii; each thread takes WD_RAD_RPT radii of one direction
+// radial plan (ball rules, mixed path): a block of WD_NPB threads covers
+// WD_NPB / NR directions x NR radii (a radius group), one radius per thread;
+// NR in {64, 128, 256} is chosen per rule (radial_group). Per tile of NR
+// triangles the block builds one record per (direction, triangle), so a
+// larger group spreads each record and each tile barrier over more pairs.
 constexpr int WD_RAD_RPT = 1;  // radii per thread; 2 (3 blocks per SM) ran 7 % faster on all-Taylor rows but 25 % slower where rows mix branches
-constexpr int WD_RAD_NR = 64;                        // radii per block
-constexpr int WD_RAD_TPD = WD_RAD_NR / WD_RAD_RPT;   // threads per direction
-constexpr int WD_RAD_ND = WD_NPB / WD_RAD_TPD;       // directions per block
-constexpr int WD_RAD_TILE = WD_NPB / WD_RAD_ND;      // triangles per record tile (one record per thread)
+template <int NR>
+struct RadShape {
+    static_assert(NR == 64 || NR == 128 || NR == 256, "radius group of 64, 128 or 256");
+    static constexpr int TPD = NR / WD_RAD_RPT;  // threads per direction
+    static constexpr int ND = WD_NPB / TPD;      // directions per block
+    static constexpr int TILE = WD_NPB / ND;     // triangles per record tile (one record per thread)
+    static constexpr int IDX = NR == 64 ? 0 : (NR == 128 ? 1 : 2);
+};
 
 size_t wd_tri_record_bytes(int precision);
 // stage triangles (a1): records for mu (sign +1) at offset 0 and optionally a

@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(WD_NPB) pair_kernel_lattice(const PairArgs a, 
 // tail Psi - 1/2 = sr + i si is a polynomial in rho = r^2:
 //     sr = rho (R1 + rho (R2 + ... + rho R6)),  si = r^3 (I0 + rho (I1 + ... + rho I4)),
 // the same terms (h_n to n = 12) as the per-node kernel, regrouped by powers of
-// r. A block covers WD_RAD_ND directions x WD_RAD_NR radii; for each tile of
+// r. A block covers WD_NPB / NR directions x NR radii (RadShape); for each tile of
 // triangles it first computes one record of rates and coefficients per
 // (direction, triangle), in float32 (float pairs for the phase rate: the
 // float64 pipe of this GPU is too narrow for it), then every thread runs
@@ -1243,10 +1243,11 @@ __device__ __forceinline__ void taylor_combine_half(float c, float s, float ar, 
     fi = fmaf(g2, s, fmaf(s, ar, c * ai));
 }
 
-// One thread's nodes in a radial node block: block nb covers directions
-// [dg WD_RAD_ND, +WD_RAD_ND) x radii [rg WD_RAD_NR, +WD_RAD_NR); thread t takes
-// direction t / WD_RAD_TPD (warp-uniform) and the WD_RAD_RPT radii
-// t % WD_RAD_TPD + q WD_RAD_TPD, q < WD_RAD_RPT, of the block's radius group.
+// One thread's nodes in a radial node block: with radius group NR, block nb
+// covers directions [dg ND, +ND) x radii [rg NR, +NR), ND = WD_NPB / NR;
+// thread t takes direction t / TPD (warp-uniform) and the WD_RAD_RPT radii
+// t % TPD + q TPD, q < WD_RAD_RPT, of the block's radius group, TPD = NR /
+// WD_RAD_RPT. A warp always holds 32 consecutive radii of one direction.
 struct RadThread {
     int64_t dg;
     int dl;
@@ -1262,19 +1263,21 @@ struct RadThread {
 
 // dith_base: index, in the full rule, of the first node of a radial window
 // (the dither is a function of that index, so a window's nodes keep theirs)
+template <int NR>
 __device__ __forceinline__ RadThread radial_thread(const double* __restrict__ rad, int n_rad, int64_t n_dir,
                                                    int64_t nb, int n_rg, int64_t dith_base)
 {
+    using S = RadShape<NR>;
     RadThread h;
-    h.dl = threadIdx.x / WD_RAD_TPD;
-    const int rl = threadIdx.x % WD_RAD_TPD;
+    h.dl = threadIdx.x / S::TPD;
+    const int rl = threadIdx.x % S::TPD;
     h.dg = nb / n_rg;
     const int rg = (int)(nb - h.dg * n_rg);
-    const int64_t d = h.dg * WD_RAD_ND + h.dl;
+    const int64_t d = h.dg * S::ND + h.dl;
     h.dir_ok = d < n_dir;
 #pragma unroll
     for (int q = 0; q < WD_RAD_RPT; ++q) {
-        const int ir = rg * WD_RAD_NR + rl + q * WD_RAD_TPD;
+        const int ir = rg * NR + rl + q * S::TPD;
         h.active[q] = h.dir_ok && ir < n_rad;
         h.node[q] = h.active[q] ? (int64_t)ir * n_dir + d : 0;
         const double r = h.active[q] ? rad[ir] : 0.0;
@@ -1426,19 +1429,24 @@ __device__ __forceinline__ void radial_row(const TabEntry* __restrict__ tl, cons
 }
 
 // Sums of F_T over the triangle records [t0, t1) at the thread's nodes, in
-// tiles of WD_RAD_TILE triangles: the block first fills the tile's
-// (direction, triangle) records, then every thread runs over its direction's
-// row. Called by every thread of the block (barriers inside).
-__device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const TabEntry* __restrict__ tab,
+// tiles of TILE = NR triangles: the block first fills the tile's (direction,
+// triangle) records, then every thread runs over its direction's row, in
+// segments of 64 records. Called by every thread of the block (barriers
+// inside). Every choice that shapes a node's float32 operations (the row form
+// per 64 records, the branch threshold per warp of 32 radii, groups of 8
+// pairs from t0) is independent of NR, so a node's sum is the same bits for
+// every radius group, radial window and serving batch.
+template <int NR>
+__device__ __forceinline__ void radial_sum(RadRec* tile, const TabEntry* __restrict__ tab,
                                            const TriRecF* __restrict__ tris, int64_t t0, int64_t t1,
                                            const float* __restrict__ dir, int64_t n_dir, const RadThread& h,
                                            double* acc_r, double* acc_i)
 {
-    static_assert(WD_RAD_TILE % 32 == 0 && WD_NPB % 32 == 0, "a warp builds records of one direction");
-    constexpr int kParts = WD_RAD_TILE / 32;                  // warps' worth of records per direction row
-    __shared__ unsigned int s_gmax[WD_RAD_ND * kParts];       // largest gmax0 per 32 records, as bits
-    __shared__ unsigned int s_pmax[WD_RAD_ND * kParts];       // largest |dmh| per 32 records, as bits
-    __shared__ float s_rmax[WD_NPB / 32];                     // largest active radius per warp
+    using S = RadShape<NR>;
+    static_assert(S::TILE % 64 == 0 && WD_NPB % 32 == 0, "a warp builds records of one direction");
+    __shared__ unsigned int s_gmax[WD_NPB / 32];  // largest gmax0 per 32 records, as bits
+    __shared__ unsigned int s_pmax[WD_NPB / 32];  // largest |dmh| per 32 records, as bits
+    __shared__ float s_rmax[WD_NPB / 32];         // largest active radius per warp
     {
         float rm = 0.0f;
 #pragma unroll
@@ -1451,16 +1459,17 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
     // pair (s, c) goes to float64 once, at the end: a float64 conversion per
     // tile kept this GPU's narrow float64 pipe 10 % busy)
     Kahan kr[WD_RAD_RPT], ki[WD_RAD_RPT];
-    for (int64_t tb = t0; tb < t1; tb += WD_RAD_TILE) {
-        const int cnt = (int)((t1 - tb) < WD_RAD_TILE ? (t1 - tb) : WD_RAD_TILE);
+    for (int64_t tb = t0; tb < t1; tb += S::TILE) {
+        const int cnt = (int)((t1 - tb) < S::TILE ? (t1 - tb) : S::TILE);
         const int cnt8 = (cnt + 7) & ~7;
         __syncthreads();
-        // records for WD_RAD_ND directions x cnt8 triangles (zero padding:
-        // gamma = 0, gmax0 = 0), and the largest gmax0 of every 32 of them
-        // (gmax0 >= 0, so its bits order like its value)
-        for (int i = threadIdx.x; i < WD_RAD_ND * WD_RAD_TILE; i += WD_NPB) {
-            const int di = i / WD_RAD_TILE, j = i % WD_RAD_TILE;
-            const int64_t dd = h.dg * WD_RAD_ND + di;
+        // records for ND directions x cnt8 triangles (zero padding: gamma =
+        // 0, gmax0 = 0), one per thread, and the largest gmax0 of every 32
+        // of them (gmax0 >= 0, so its bits order like its value)
+        {
+            const int i = threadIdx.x;
+            const int di = i / S::TILE, j = i % S::TILE;
+            const int64_t dd = h.dg * S::ND + di;
             float gm = 0.0f, pm = 0.0f;
             if (j < cnt8) {
                 RadRec o;
@@ -1472,7 +1481,7 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
                 }
                 gm = o.gmax0;
                 pm = fabsf(o.dmh);
-                tile[di][j] = o;
+                tile[i] = o;
             }
             const unsigned int wm = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
             const unsigned int pmx = __reduce_max_sync(0xffffffffu, __float_as_uint(pm));
@@ -1486,32 +1495,31 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
 #pragma unroll
         for (int q = 0; q < WD_RAD_RPT; ++q) any_node = any_node || h.active[q];
         if (!h.dir_ok || !__any_sync(0xffffffffu, any_node)) continue;  // warp-uniform: no node here
-        const RadRec* rec = tile[h.dl];
+        const RadRec* rec = tile + h.dl * S::TILE;
+        const float rmax = s_rmax[threadIdx.x >> 5];
         // No per-tile phase shift here: on ball rules the weight spreads over
         // many nodes and the shift's float64 rotation cost 3% of the
         // throughput without a measurable gain in accuracy (see the per-node
-        // kernel for the lattice case). Where every record of the row keeps
-        // every lane of the warp in the Taylor branch, the row runs without
-        // the per-pair branch test, and with the short series where every
-        // gap is below DELTA_S; the choice is the same for the whole warp.
-        unsigned int gu = 0u, pu = 0u;
-#pragma unroll
-        for (int p = 0; p < kParts; ++p) {
-            gu = max(gu, s_gmax[h.dl * kParts + p]);
-            pu = max(pu, s_pmax[h.dl * kParts + p]);
+        // kernel for the lattice case). Where every record of a 64-record
+        // segment keeps every lane of the warp in the Taylor branch, the
+        // segment runs without the per-pair branch test, and with the short
+        // series where every gap is below DELTA_S; the choice is the same for
+        // the whole warp.
+        for (int seg = 0; seg < cnt8; seg += 64) {
+            const int n8 = cnt8 - seg < 64 ? cnt8 - seg : 64;
+            const int k = (h.dl * S::TILE + seg) >> 5;  // the segment's two 32-record maxima
+            const float gap = __uint_as_float(max(s_gmax[k], s_gmax[k + 1])) * rmax;  // bounds every lane's gaps
+            // the table exponential takes the unreduced phase while |128 P|
+            // stays well inside the magic constant's 2^22 integer range
+            if (__uint_as_float(max(s_pmax[k], s_pmax[k + 1])) * rmax >= 8192.0f)
+                radial_row<3>(tl, rec + seg, n8, h, kr, ki);
+            else if (gap < kDeltaShort32)
+                radial_row<2>(tl, rec + seg, n8, h, kr, ki);
+            else if (gap < kDelta32)
+                radial_row<1>(tl, rec + seg, n8, h, kr, ki);
+            else
+                radial_row<0>(tl, rec + seg, n8, h, kr, ki);
         }
-        const float rmax = s_rmax[threadIdx.x >> 5];
-        const float gap_row = __uint_as_float(gu) * rmax;  // bounds every lane's gaps
-        // the table exponential takes the unreduced phase while |128 P| stays
-        // well inside the magic constant's 2^22 integer range
-        if (__uint_as_float(pu) * rmax >= 8192.0f)
-            radial_row<3>(tl, rec, cnt8, h, kr, ki);
-        else if (gap_row < kDeltaShort32)
-            radial_row<2>(tl, rec, cnt8, h, kr, ki);
-        else if (gap_row < kDelta32)
-            radial_row<1>(tl, rec, cnt8, h, kr, ki);
-        else
-            radial_row<0>(tl, rec, cnt8, h, kr, ki);
     }
 #pragma unroll
     for (int q = 0; q < WD_RAD_RPT; ++q) {
@@ -1521,24 +1529,25 @@ __device__ __forceinline__ void radial_sum(RadRec (*tile)[WD_RAD_TILE], const Ta
 }
 
 struct RadSmem {
-    RadRec tile[WD_RAD_ND][WD_RAD_TILE];
+    RadRec tile[WD_NPB];  // ND directions x TILE triangles, direction-major
     TabEntry etab[kTab * kTabRep];
 };
 
 // One work item (radial node block nb, triangle chunk) of the radial form.
 // Called by every thread of the block (barriers inside); etab is filled.
-template <int MODE>
+template <int MODE, int NR>
 __device__ __forceinline__ void radial_item(const PairArgs& a, const PairPlan& p, int64_t item, RadSmem& sm,
                                             double* red, int& s_last)
 {
     const int64_t nb = item / p.nchunks;
     const int chunk = (int)(item - nb * p.nchunks);
-    const RadThread h = radial_thread(a.rad, a.n_rad, a.n_dir, nb, p.n_rg, a.dith_base);
+    const RadThread h = radial_thread<NR>(a.rad, a.n_rad, a.n_dir, nb, p.n_rg, a.dith_base);
     const int64_t t0 = (int64_t)chunk * p.tiles_per_chunk * WD_TILE;
     int64_t t1 = t0 + (int64_t)p.tiles_per_chunk * WD_TILE;
     if (t1 > a.T) t1 = a.T;
     double acc_r[WD_RAD_RPT], acc_i[WD_RAD_RPT];
-    radial_sum(sm.tile, sm.etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r, acc_i);
+    radial_sum<NR>(sm.tile, sm.etab, static_cast<const TriRecF*>(a.tris), t0, t1, a.dir, a.n_dir, h, acc_r,
+                   acc_i);
     float dith[WD_RAD_RPT];  // j / kTab turns, exact
 #pragma unroll
     for (int q = 0; q < WD_RAD_RPT; ++q) dith[q] = kMagicTurns - h.mt[q];
@@ -1547,7 +1556,7 @@ __device__ __forceinline__ void radial_item(const PairArgs& a, const PairPlan& p
                                                  s_last, ps, h.node);
 }
 
-template <int MODE>
+template <int MODE, int NR>
 __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) pair_kernel_radial(const PairArgs a,
                                                                                       const PairPlan p)
 {
@@ -1556,7 +1565,7 @@ __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) pair_kernel_r
     __shared__ int s_last;
     fill_exp_table(sm.etab);  // visible after the first tile barrier
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x)
-        radial_item<MODE>(a, p, item, sm, red, s_last);
+        radial_item<MODE, NR>(a, p, item, sm, red, s_last);
 }
 
 template <bool MIXED, int MODE>
@@ -1591,17 +1600,41 @@ int resident_precise_for(wd_ctx* ctx, int mode)
     return resident_precise<MODE_DIST>(ctx);
 }
 
-template <int MODE>
+template <int MODE, int NR>
 int resident_radial(wd_ctx* ctx)
 {
-    return wd_resident(ctx, OCC_RADIAL + MODE, pair_kernel_radial<MODE>, WD_NPB);
+    return wd_resident(ctx, OCC_RADIAL + 3 * MODE + RadShape<NR>::IDX, pair_kernel_radial<MODE, NR>, WD_NPB);
 }
 
-int resident_radial_for(wd_ctx* ctx, int mode)
+template <int MODE>
+int resident_radial_mode(wd_ctx* ctx, int nr)
 {
-    if (mode == MODE_FT) return resident_radial<MODE_FT>(ctx);
-    if (mode == MODE_RESID) return resident_radial<MODE_RESID>(ctx);
-    return resident_radial<MODE_DIST>(ctx);
+    if (nr == 256) return resident_radial<MODE, 256>(ctx);
+    if (nr == 128) return resident_radial<MODE, 128>(ctx);
+    return resident_radial<MODE, 64>(ctx);
+}
+
+// The radius group for a ball rule with n_rad radii: the one that leaves the
+// fewest idle threads, the larger on a tie.
+int radial_group(int n_rad)
+{
+    int best = 64;
+    int64_t best_slots = 0;
+    for (int nr : {64, 128, 256}) {
+        const int64_t slots = (int64_t)((n_rad + nr - 1) / nr) * nr;  // threads per direction
+        if (best_slots == 0 || slots <= best_slots) {
+            best = nr;
+            best_slots = slots;
+        }
+    }
+    return best;
+}
+
+int resident_radial_for(wd_ctx* ctx, int mode, int nr)
+{
+    if (mode == MODE_FT) return resident_radial_mode<MODE_FT>(ctx, nr);
+    if (mode == MODE_RESID) return resident_radial_mode<MODE_RESID>(ctx, nr);
+    return resident_radial_mode<MODE_DIST>(ctx, nr);
 }
 
 // Split the triangle range into chunks only when the node blocks alone cannot
@@ -1666,6 +1699,15 @@ __device__ __forceinline__ const ServeRange& serve_find_range(const ServeRange* 
     return rg[lo];
 }
 
+// one radial work item of a served request, compiled on its own (a call per
+// item) so that the three radius groups do not share one register allocation
+template <int NR>
+__device__ __noinline__ void serve_radial_item(const ServeReq& rq, int64_t item, RadSmem& sm, double* red,
+                                               int& s_last)
+{
+    radial_item<MODE_DIST, NR>(rq.a, rq.p, item, sm, red, s_last);
+}
+
 __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel_radial(
     ServeTable* __restrict__ head, const ServeRange* __restrict__ ranges, const ServeReq* __restrict__ reqs)
 {
@@ -1681,7 +1723,13 @@ __global__ void __launch_bounds__(WD_NPB, WD_RAD_RPT == 1 ? 4 : 3) serve_kernel_
         if (it >= n_items) break;
         const ServeRange& r = serve_find_range(ranges, n_rg, it);
         const ServeReq& rq = reqs[r.req];
-        radial_item<MODE_DIST>(rq.a, rq.p, r.first + (it - r.start), sm, red, s_last);
+        const int64_t item = r.first + (it - r.start);
+        if (rq.p.rad_nr == 256)  // block-uniform: the request's radius group
+            serve_radial_item<256>(rq, item, sm, red, s_last);
+        else if (rq.p.rad_nr == 128)
+            serve_radial_item<128>(rq, item, sm, red, s_last);
+        else
+            serve_radial_item<64>(rq, item, sm, red, s_last);
     }
 }
 
@@ -1817,12 +1865,14 @@ wd_status wd_plan_pair_rule(wd_ctx* ctx, const wd_rule* rule, int precision, int
         return wd_plan_pair(ctx, precision, mode, rule->n_eval, n_tris, plan);
     PairPlan p;
     p.radial = true;
+    p.rad_nr = radial_group(rule->n_rad);
+    const int nd = WD_NPB / p.rad_nr;  // directions per block
     p.n_nodes = rule->n_eval;
     p.n_tris = n_tris;
-    p.n_dg = (rule->n_dir + WD_RAD_ND - 1) / WD_RAD_ND;
-    p.n_rg = (rule->n_rad + WD_RAD_NR - 1) / WD_RAD_NR;
+    p.n_dg = (rule->n_dir + nd - 1) / nd;
+    p.n_rg = (rule->n_rad + p.rad_nr - 1) / p.rad_nr;
     p.n_nb = p.n_dg * p.n_rg;
-    plan_chunks(p, resident_radial_for(ctx, mode));
+    plan_chunks(p, resident_radial_for(ctx, mode, p.rad_nr));
     *plan = p;
     return WD_OK;
 }
@@ -1867,6 +1917,24 @@ void wd_pair_args_rule(const wd_rule* rule, PairArgs& a)
     a.lat_hl = rule->lat_hl;
 }
 
+template <int MODE>
+void launch_radial_mode(const PairPlan& plan, const PairArgs& args, cudaStream_t st)
+{
+    if (plan.rad_nr == 256)
+        pair_kernel_radial<MODE, 256><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+    else if (plan.rad_nr == 128)
+        pair_kernel_radial<MODE, 128><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+    else
+        pair_kernel_radial<MODE, 64><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+}
+
+void launch_radial(int mode, const PairPlan& plan, const PairArgs& args, cudaStream_t st)
+{
+    if (mode == MODE_FT) launch_radial_mode<MODE_FT>(plan, args, st);
+    else if (mode == MODE_RESID) launch_radial_mode<MODE_RESID>(plan, args, st);
+    else launch_radial_mode<MODE_DIST>(plan, args, st);
+}
+
 wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& plan,
                          const PairArgs& args, cudaStream_t st)
 {
@@ -1876,9 +1944,7 @@ wd_status wd_launch_pair(wd_ctx* ctx, int precision, int mode, const PairPlan& p
             wd_set_error("internal: radial plan without a mixed ball rule");
             return WD_EINVAL;
         }
-        if (mode == MODE_FT) pair_kernel_radial<MODE_FT><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
-        else if (mode == MODE_RESID) pair_kernel_radial<MODE_RESID><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
-        else pair_kernel_radial<MODE_DIST><<<plan.grid, WD_NPB, 0, st>>>(args, plan);
+        launch_radial(mode, plan, args, st);
     } else if (precision == WD_MIXED) {
         if (plan.lattice) {
             if (!args.lines || !args.lblk) {
