@@ -48,10 +48,11 @@ L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
 # From ncu captures of the current radial pair kernel (set to None when the
 # kernel changes): DRAM bytes (read + write) of one large-query launch, and the
 # thread instructions per pair and issue-active fraction of its full-set
-# capture on a 64-shell window of the same rule.
-PAIR_KERNEL_TRAFFIC_LARGE = 129.71e6 + 6.37e6
-PAIR_KERNEL_INSTR_PER_PAIR = 56.2
-PAIR_KERNEL_ISSUE_ACTIVE = 0.771
+# capture on the large mesh with every radial shell of the large rule and 1/16
+# of its directions (the same 256-radius blocks).
+PAIR_KERNEL_TRAFFIC_LARGE = 129.88e6 + 6.03e6
+PAIR_KERNEL_INSTR_PER_PAIR = 47.1
+PAIR_KERNEL_ISSUE_ACTIVE = 0.789
 # radial shells of the large rule whose D is recomputed in float64 after the
 # timed region (a 32-aligned window evaluates every node with the same float32
 # operations as the full launch)
@@ -75,11 +76,13 @@ def parse():
     p.add_argument("--serve-queries", type=int, default=2000)
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint batch and fitting measurement")
     p.add_argument("--no-paper", action="store_true", help="skip the paper's cube-rule refinement ladder")
-    p.add_argument("--case", choices=["adjoint-n16", "large-window", "large"], default=None,
+    p.add_argument("--case", choices=["adjoint-n16", "large-window", "large-dirs", "large"], default=None,
                    help="run one fixed case for a profiler and exit: adjoint-n16 = three mixed gradients of the "
                         "n=16 adjoint-configuration mesh (seed 0) on the 192x64x96 rule; large-window = two "
-                        "mixed distances of the large query on radial shells 128-191 of its rule; large = two "
-                        "mixed distances of the large query")
+                        "mixed distances of the large query on radial shells 128-191 of its rule; large-dirs = "
+                        "two mixed distances of the large mesh on every radial shell of the large rule with "
+                        "1/16 of its directions (256 x 32 x 64 Hermitian: the same 256-radius blocks and row "
+                        "forms as the large launch); large = two mixed distances of the large query")
     return p.parse_args()
 
 
@@ -618,10 +621,12 @@ def profile_case(name):
             wd.wd_distance_grad_dev(ctx.handle, rule, dv, dt, None, 1.0, wd.WD_MIXED, out, g)
         torch.cuda.synchronize()
         print("D %.12e |grad| %.12e" % (out.item(), g.norm().item()))
-    elif name in ("large-window", "large"):
+    elif name in ("large-window", "large-dirs", "large"):
         R = synth.LARGE_RULE
         if name == "large":
             rule = ctx.rule(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian)
+        elif name == "large-dirs":
+            rule = ctx.rule(R.R, R.n_r, R.n_polar // 4, R.n_azim // 4, R.hermitian)
         else:
             rule = ctx.rule_shells(R.R, R.n_r, R.n_polar, R.n_azim, R.hermitian, 128, 192)
         v, t = synth.large_mesh()
@@ -787,7 +792,8 @@ def main():
             "traffic_note": "dram read+write bytes of one large-query launch of pair_kernel_radial (ncu, 1-pass "
                             "metrics, the current kernel); algorithmic bytes of that launch: W and nu^ per node "
                             "(24 B x 4,194,304) + mesh records (64 B x 327,680) = 121.6 MB; instructions per pair "
-                            "and issue from the full-set capture of the same kernel on shells 128-191",
+                            "and issue from the full-set capture of the same kernel on the large mesh with the "
+                            "rule's 256 shells and 1/16 of its directions",
             "kernel": "pair_kernel_radial (mixed, distance mode)" if prec == wd.WD_MIXED else "pair_kernel (fp64)",
             "peak_basis": "%d SMs x %.0f MHz (%s) / max(%d FP32 ops/128, %d MUFU ops/16) clk per pair"
                           % (sm_count, peaks.get("sm_max_mhz", 2032.0), peak_src, N_FP32_PER_PAIR,
