@@ -208,6 +208,26 @@ __device__ __forceinline__ void expm_residual(const TabEntry* __restrict__ tl, i
     ei = -s;
 }
 
+// expm_residual for |v| <= 1/128 + a few 2^-24 (two table steps): the sine to
+// v^5 and the cosine to v^6 (the first dropped terms below 1.5e-13), for a
+// kernel whose residual is the sum of two table-step residuals.
+__device__ __forceinline__ void expm_residual_wide(const TabEntry* __restrict__ tl, int idx, float v, float& er,
+                                                   float& ei)
+{
+    const float v2 = v * v;
+    // cos 2 pi v - 1 = -(2 pi)^2 v^2 / 2 + (2 pi)^4 v^4 / 24 - (2 pi)^6 v^6 / 720 and
+    // sin 2 pi v = 2 pi v - (2 pi)^3 v^3 / 6 + (2 pi)^5 v^5 / 120, the leading constants split
+    const float dc = fmaf(v2, -19.7392082214355469f,
+                          v2 * fmaf(v2, fmaf(v2, -85.4568172066937f, 64.9393940226682914f), -5.80743176215037e-07f));
+    const float sx = fmaf(v, 6.28318548202514648f,
+                          v * fmaf(v2, fmaf(v2, 81.6052492760750f, -41.3417022403997534f), -1.74845553146951715e-07f));
+    const TabEntry t = tl[idx * kTabRep];
+    const float c = t.ch + fmaf(t.ch, dc, fmaf(-t.sh, sx, t.cl));
+    const float s = t.sh + fmaf(t.sh, dc, fmaf(t.ch, sx, t.sl));
+    er = c;
+    ei = -s;
+}
+
 __device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl, float tau, float tlo, float& er,
                                                 float& ei, float magic = kMagic)
 {

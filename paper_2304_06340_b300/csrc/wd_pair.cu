@@ -246,7 +246,20 @@ __device__ __forceinline__ void pair_mixed_divdiff(const TabEntry* __restrict__ 
 // every time, and it has one sign (-p/24), so the loss would be a bias. It is
 // added inside the final rounding with gamma, where gamma c/2 is a full-width
 // product off the float grid.
-// FAST: expm_turns_fast (the lattice kernel's series rows)
+// gamma (c + i s)(1/2 + sr + i si) = g2 (c + i s) + (c + i s)(ar + i ai) with
+// g2 = gamma/2, ar = gamma sr + gamma_lo/2, ai = gamma si, (c, s) = exp(-i t);
+// gamma_lo times the tail (2^-24 of a zero-mean term) is left out
+__device__ __forceinline__ void taylor_gamma(float c, float s, float sr, float si, float gam, float gam_lo, float& fr,
+                                             float& fi)
+{
+    const float g2 = 0.5f * gam;  // exact
+    const float ar = fmaf(gam, sr, 0.5f * gam_lo);
+    const float ai = gam * si;
+    fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
+    fi = fmaf(g2, s, fmaf(s, ar, c * ai));
+}
+
+// FAST: expm_turns_fast
 template <bool FAST = false>
 __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab, float tau, float tlo, float sr,
                                                float si, float gam, float gam_lo, float& fr, float& fi, float magic)
@@ -255,14 +268,7 @@ __device__ __forceinline__ void taylor_combine(const TabEntry* __restrict__ tab,
     // (c, s) = exp(-i (t_m - 2 pi dith + 2 pi shift))
     if (FAST) expm_turns_fast(tab, tau, tlo, c, s, magic);
     else expm_turns(tab, tau, tlo, c, s, magic);
-    // gamma (c + i s)(1/2 + sr + i si) = g2 (c + i s) + (c + i s)(ar + i ai) with
-    // g2 = gamma/2, ar = gamma sr + gamma_lo/2, ai = gamma si; gamma_lo times
-    // the tail (2^-24 of a zero-mean term) is left out
-    const float g2 = 0.5f * gam;                    // exact
-    const float ar = fmaf(gam, sr, 0.5f * gam_lo);
-    const float ai = gam * si;
-    fr = fmaf(g2, c, fmaf(c, ar, -s * ai));
-    fi = fmaf(g2, s, fmaf(s, ar, c * ai));
+    taylor_gamma(c, s, sr, si, gam, gam_lo, fr, fi);
 }
 
 __device__ __forceinline__ void pair_mixed_gaps(const TabEntry* __restrict__ tab, float tau, float tlo, float g1,
@@ -835,15 +841,20 @@ __device__ __forceinline__ float line_node_dither(uint32_t d0u, uint32_t du, int
 
 // Per-(line, triangle) record, grouped by 16 bytes in the order the rows read
 // them: the series rows read groups 0-3, the per-pair rows 0, 1 (gamma), 3, 4.
+// The dithered phase at i = 0 is the float pair t0h + t0l, t0h reduced mod 1,
+// held as t0h = S0 / kTab + t0r (S0 whole table steps, |t0r| <= 1/256): mt0 =
+// kMagicTurns + S0 / kTab is the magic constant of the series rows' table
+// lookup, which then adds the steps of t0h to those of i rh for free.
 struct __align__(16) LatRec {
-    float t0h, t0l;        // dithered phase at i = 0 (turns, reduced mod 1), float pair
+    float mt0, t0r;        // kMagicTurns + S0 / kTab (exact) and t0h - S0 / kTab
     float rh, rl;          // dithered phase per step of i, float pair
     float A0, A1, A2;      // A(i) = A0 + A1 i + A2 i^2
     float gam;             // twice the area, high part (0 for padding)
     float Q0, Q1, Q2, Q3;  // q(i) = y_a y_b y_c
     float gam_lo;
     float gmax;            // bound of the largest |gap| over the block's nodes on this line
-    float pad[2];
+    float t0l;             // low part of the phase at i = 0
+    float pad;
     float G1, d1, G2, d2;  // gaps g1 = G1 + i d1, g2 = G2 + i d2 (radians)
 };
 static_assert(sizeof(LatRec) == 80, "LatRec layout");
@@ -868,8 +879,11 @@ __device__ __forceinline__ void make_latrec(const TriRecF& t, const LatLine& ln,
     const float f2 = f - d0;
     lo += two_sum_err(f, -d0, f2);
     f = f2 - rintf(f2);
-    o.t0h = f + lo;
-    o.t0l = lo - (o.t0h - f);
+    const float t0h = f + lo;
+    o.t0l = lo - (t0h - f);
+    const float S0 = rintf(t0h * (float)kTab);  // |S0| <= kTab / 2
+    o.mt0 = kMagicTurns + S0 * (1.0f / kTab);     // exact
+    o.t0r = fmaf(S0, -1.0f / kTab, t0h);          // exact
     // rate per step of i: h m_x - du 2^-20
     const float pr = hh * t.mh[0];
     float rlo = fmaf(hh, t.mh[0], -pr) + fmaf(hh, t.ml[0], hl * t.mh[0]);
@@ -904,7 +918,7 @@ __device__ __forceinline__ void make_latrec(const TriRecF& t, const LatLine& ln,
     gm = fmaxf(gm, fmaxf(fabsf(fmaf(fa, o.d2, o.G2)), fabsf(fmaf(fb, o.d2, o.G2))));
     gm = fmaxf(gm, fmaxf(fabsf(fmaf(fa, d3, G3)), fabsf(fmaf(fb, d3, G3))));
     o.gmax = t.gam != 0.0f ? gm : 0.0f;
-    o.pad[0] = o.pad[1] = 0.0f;
+    o.pad = 0.0f;
 }
 
 struct LatSmem {
@@ -926,11 +940,11 @@ __device__ __forceinline__ void lattice_row(const TabEntry* __restrict__ tl, con
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
             const LatRec& t = rec[j + jj];
-            const float P = fi * t.rh;
-            const float lo = fmaf(fi, t.rl, fmaf(fi, t.rh, -P) + t.t0l);
-            const float tau = (P - rintf(P)) + t.t0h;
             float fr, fim;
             if (VAR == 0) {
+                const float P = fi * t.rh;
+                const float lo = fmaf(fi, t.rl, fmaf(fi, t.rh, -P) + t.t0l);
+                const float tau = (P - rintf(P)) + ((t.mt0 - kMagicTurns) + t.t0r);  // t0h, exact
                 pair_mixed_gaps(tl, tau, lo, fmaf(fi, t.d1, t.G1), fmaf(fi, t.d2, t.G2), t.gam, t.gam_lo, fr, fim,
                                 magic);
             } else {
@@ -963,7 +977,19 @@ __device__ __forceinline__ void lattice_row(const TabEntry* __restrict__ tl, con
                     const float iq = fmaf(p, 4.0f / 6227020800.0f, -1.0f / 39916800.0f);
                     si = qq * fmaf(q2, iq, im);
                 }
-                taylor_combine<true>(tl, tau, lo, sr, si, t.gam, t.gam_lo, fr, fim, magic);
+                // the phase i (rh + rl) + t0h + t0l with its reduction in the
+                // table lookup: adding mt0 to the exact product i rh rounds it
+                // to K table steps and leaves the index K + S0 in the low bits;
+                // mt0 minus that sum is -K / kTab exactly, one more FMA gives
+                // the residual i rh - K / kTab with a single rounding, and t0r
+                // (at most one more table step) joins it
+                const float m = fmaf(fi, t.rh, t.mt0);
+                const int idx = __float_as_int(m) & (kTab - 1);
+                const float u = fmaf(fi, t.rh, t.mt0 - m);
+                const float v = (u + t.t0r) + fmaf(fi, t.rl, t.t0l);
+                float c, s;
+                expm_residual_wide(tl, idx, v, c, s);
+                taylor_gamma(c, s, sr, si, t.gam, t.gam_lo, fr, fim);
             }
             br += fr;
             bi += fim;

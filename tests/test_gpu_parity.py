@@ -267,3 +267,26 @@ def test_radial_shell_windows(ctx):
         assert e.value.status == wd.WD_EINVAL
     with pytest.raises(wd.WDError):
         wd.wd_build_freq_rule_shells(ctx.handle, 5.0, 16, 0, 0, True, 0, 4)  # no windows of n_polar = 0
+
+
+def test_far_mesh_reaches_the_reduced_phase_rows(ctx):
+    """A mesh 1000 units from the origin on a ball rule at R = 64: its phases
+    reach 10^4 turns, past the 2^13 turns up to which the radial kernel feeds
+    the unreduced phase to the table lookup, so the outer rows take the form
+    that reduces the phase mod 1 first, and the inner ones use the lookup near
+    the top of its range. A common translation c of the mesh and the sphere
+    multiplies both transforms by exp(-i xi.c) (translation theorem), so D is
+    unchanged: the translated D must equal the untranslated float64 D, and
+    the mixed D must stay within the 1e-6 bar of it."""
+    desc = (64.0, 64, 32, 64, True)
+    rule = ctx.rule(*desc)
+    v, t = synth.icosphere(16)
+    v = synth.jitter_isotropic(v, 0.01, 5)
+    c = np.array([600.0, 800.0, 0.0])
+    d0 = ctx.distance(rule, v, t, None, 1.0, FP64)
+    d64 = ctx.distance(rule, v + c, t, ("sphere", 1.0, c), 1.0, FP64)
+    dmx = ctx.distance(rule, v + c, t, ("sphere", 1.0, c), 1.0, MIXED)
+    assert abs(d64 - d0) < 1e-8 * d0, (d64, d0)
+    assert abs(dmx - d0) < 1e-6 * d0, (dmx, d0, (dmx - d0) / d0)
+    assert abs(dmx - ctx.distance(rule, v, t, None, 1.0, MIXED)) < 1e-6 * d0
+
