@@ -724,12 +724,16 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
     __shared__ double acc[10][ADJ_TT];
     __shared__ float4 tres[ADJ_TT];  // a direction's results per triangle: (T0, Ti, T1, T2)
     __shared__ TabEntry etab[kTab * kTabRep];
+    __shared__ int s_rbits;  // the largest radius, as bits (radii are positive)
     fill_exp_table(etab);
     const TabEntry* tl = exp_table_lane(etab);
+    if (threadIdx.x == 0) s_rbits = 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < n_rad; i += ADJ_TPB) {
         const double r = rad[i];
         AdjRad a;
         a.rh = (float)r;
+        atomicMax(&s_rbits, __float_as_int(a.rh));  // read after the item loop's first barrier
         a.rlo = (float)(r - (double)a.rh);
         a.rho = (float)(r * r);
         a.r3 = (float)(r * r * r);
@@ -796,6 +800,11 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
             for (int j = warp; j < ADJ_TT; j += ADJ_TPB / 32) {
                 if (tri0 + j >= nt) break;  // warp-uniform
                 const AdjDirTri& q = srec[j].q;
+                // phases of 2^13 turns or more (a mesh far from the origin):
+                // lo, the high product's rounding error and the low products,
+                // can then reach table steps and is folded into tau with its
+                // exact rounding error (warp-uniform)
+                const bool big = fabsf(q.dmh) * __int_as_float(s_rbits) >= 8192.0f;
                 float S0h = 0.0f, S0t = 0.0f, Sih = 0.0f, Sit = 0.0f, SA = 0.0f, SB = 0.0f;
                 float xP = 0.0f, yP = 0.0f, xQ = 0.0f, yQ = 0.0f, G0 = 0.0f;
                 for (int ir = lane; ir < n_rad; ir += 32) {
@@ -804,8 +813,13 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
                     const float rr = w.x, ri = w.y;
                     const float P = a.rh * q.dmh;
                     const float e = fmaf(a.rh, q.dmh, -P);
-                    const float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
-                    const float tau = (P - rintf(P)) - w.z;
+                    float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
+                    float tau = (P - rintf(P)) - w.z;
+                    if (big) {
+                        const float tl2 = tau + lo;
+                        lo = two_sum_err(tau, lo, tl2);
+                        tau = tl2;
+                    }
                     if (q.gmax0 < a.thr) {
                         float c, s;
                         expm_turns_fast(tl, tau, lo, c, s);

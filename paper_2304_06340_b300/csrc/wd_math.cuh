@@ -276,6 +276,13 @@ __device__ __forceinline__ void unshift_add(const TabEntry* __restrict__ tab, in
 // Kahan-compensated float32 accumulation: the per-tile sum of nearly equal
 // terms at low frequency would otherwise round the same way at neighbouring
 // nodes, a coherent error that the mesh-minus-sphere difference magnifies.
+// rounding error of s = fl(a + b): a + b = s + err exactly (Knuth's two-sum)
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float bb = s - a;
+    return (a - (s - bb)) + (b - bb);
+}
+
 struct Kahan {
     float s = 0.0f, c = 0.0f;
     __device__ __forceinline__ void add(float x)

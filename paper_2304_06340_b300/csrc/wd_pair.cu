@@ -364,12 +364,6 @@ __device__ __forceinline__ void pair_mixed_gaps(const TabEntry* __restrict__ tab
 // arithmetic, and the largest-gap branch (large |xi| h, where mu^ - nu^ is not
 // small) is the float32 one.
 
-// rounding error of s = fl(a + b): a + b = s + err exactly (Knuth's two-sum)
-__device__ __forceinline__ float two_sum_err(float a, float b, float s)
-{
-    const float bb = s - a;
-    return (a - (s - bb)) + (b - bb);
-}
 
 // float32 sum carried as (s, c) with every addend's rounding error kept in c;
 // an addend's low part goes to c directly
@@ -1409,6 +1403,14 @@ __device__ __forceinline__ void radial_pair(const TabEntry* __restrict__ tl, con
     float P, lo;
     radial_phase(t, h, q, P, lo);
     P -= rintf(P);  // exact
+    if (REDUCE) {
+        // at these phases lo (the high product's rounding error and the low
+        // products) can reach table steps: fold it into the reduced phase
+        // with its exact rounding error, so that the residual stays small
+        const float Pl = P + lo;
+        lo = two_sum_err(P, lo, Pl);
+        P = Pl;
+    }
     if (REDUCE && t.gmax0 < h.thr[q]) {
         float ar, ai, c, s;
         radial_tail<false>(t, h, q, ar, ai);

@@ -80,3 +80,19 @@ def test_autograd_function(ctx):
     _, g = ctx.distance_grad(rule, v, t, None, 1.0, wd.WD_FP64)
     assert abs(D.item() - ctx.distance(rule, v, t)) <= 1e-14 * D.item()
     assert np.allclose(dv.grad.cpu().numpy(), 3.0 * g, rtol=1e-12, atol=1e-14)
+
+
+def test_gradient_of_a_far_mesh(ctx):
+    """A common translation c of the mesh and the sphere leaves D, and so its
+    vertex gradient, unchanged (translation theorem). At |c| = 1e3 and 1e5 the
+    radial adjoint's phases reach 1e4 and 1e6 turns, where it folds the
+    phase's rounding error into the reduced phase; its gradient must match
+    the untranslated float64 gradient at the mixed bar."""
+    v, t = synth.icosphere(8)
+    v = synth.jitter_isotropic(v, 0.01, 11)
+    rule = ctx.rule(64.0, 64, 16, 32, True)
+    d0, g0 = ctx.distance_grad(rule, v, t, None, 1.0, wd.WD_FP64)
+    for c in (np.array([600.0, 800.0, 0.0]), np.array([0.0, 6.0e4, -8.0e4])):
+        d, g = ctx.distance_grad(rule, v + c, t, ("sphere", 1.0, c), 1.0, wd.WD_MIXED)
+        assert abs(d - d0) < 1e-6 * d0, (c, d, d0)
+        assert np.linalg.norm(g - g0) < 1e-6 * np.linalg.norm(g0), (c, np.linalg.norm(g - g0) / np.linalg.norm(g0))

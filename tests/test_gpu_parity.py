@@ -270,8 +270,8 @@ def test_radial_shell_windows(ctx):
 
 
 def test_far_mesh_reaches_the_reduced_phase_rows(ctx):
-    """A mesh 1000 units from the origin on a ball rule at R = 64: its phases
-    reach 10^4 turns, past the 2^13 turns up to which the radial kernel feeds
+    """Meshes 10^3 and 10^5 units from the origin on a ball rule at R = 64: their
+    phases reach 10^4 and 10^6 turns, past the 2^13 turns up to which the radial kernel feeds
     the unreduced phase to the table lookup, so the outer rows take the form
     that reduces the phase mod 1 first, and the inner ones use the lookup near
     the top of its range. A common translation c of the mesh and the sphere
@@ -282,11 +282,15 @@ def test_far_mesh_reaches_the_reduced_phase_rows(ctx):
     rule = ctx.rule(*desc)
     v, t = synth.icosphere(16)
     v = synth.jitter_isotropic(v, 0.01, 5)
-    c = np.array([600.0, 800.0, 0.0])
     d0 = ctx.distance(rule, v, t, None, 1.0, FP64)
-    d64 = ctx.distance(rule, v + c, t, ("sphere", 1.0, c), 1.0, FP64)
-    dmx = ctx.distance(rule, v + c, t, ("sphere", 1.0, c), 1.0, MIXED)
-    assert abs(d64 - d0) < 1e-8 * d0, (d64, d0)
-    assert abs(dmx - d0) < 1e-6 * d0, (dmx, d0, (dmx - d0) / d0)
-    assert abs(dmx - ctx.distance(rule, v, t, None, 1.0, MIXED)) < 1e-6 * d0
+    dmx0 = ctx.distance(rule, v, t, None, 1.0, MIXED)
+    # |c| = 1e3: phases to 1e4 turns; |c| = 1e5: to 1e6 turns, where the high
+    # product's rounding error alone spans table steps
+    # (float64 itself rounds phases of 6e6 rad at 7e-10 rad: 1e-7 there)
+    for c, tol64 in ((np.array([600.0, 800.0, 0.0]), 1e-8), (np.array([0.0, 6.0e4, -8.0e4]), 1e-7)):
+        d64 = ctx.distance(rule, v + c, t, ("sphere", 1.0, c), 1.0, FP64)
+        dmx = ctx.distance(rule, v + c, t, ("sphere", 1.0, c), 1.0, MIXED)
+        assert abs(d64 - d0) < tol64 * d0, (c, d64, d0)
+        assert abs(dmx - d0) < 1e-6 * d0, (c, dmx, d0, (dmx - d0) / d0)
+        assert abs(dmx - dmx0) < 1e-6 * d0, (c, dmx, dmx0)
 
