@@ -705,6 +705,70 @@ struct __align__(16) AdjRec {
 };
 static_assert(sizeof(AdjRec) % 16 == 0, "AdjRec layout");
 
+// One lane's radii of a (direction, triangle) record in the radial adjoint:
+// lane l takes radii l, l + 32, ... and adds into its partial sums. BIG folds
+// the phase's rounding error into the reduced phase (phases of 2^13 turns or
+// more, where it can reach table steps); the record decides, warp-uniformly.
+template <bool BIG>
+__device__ __forceinline__ void adj_lane_radii(const AdjRad* __restrict__ rt, const float4* __restrict__ sn,
+                                               const AdjRec& rec, const TabEntry* __restrict__ tl, int lane, int n_rad,
+                                               float& S0h, float& S0t, float& Sih, float& Sit, float& SA, float& SB,
+                                               float& xP, float& yP, float& xQ, float& yQ, float& G0)
+{
+    const AdjDirTri& q = rec.q;
+    for (int ir = lane; ir < n_rad; ir += 32) {
+        const AdjRad a = rt[ir];
+        const float4 w = sn[ir];
+        const float rr = w.x, ri = w.y;
+        const float P = a.rh * q.dmh;
+        const float e = fmaf(a.rh, q.dmh, -P);
+        float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
+        float tau = (P - rintf(P)) - w.z;
+        if (BIG) {
+            const float tl2 = tau + lo;
+            lo = two_sum_err(tau, lo, tl2);
+            tau = tl2;
+        }
+        if (q.gmax0 < a.thr) {
+            float c, s;
+            expm_turns_fast(tl, tau, lo, c, s);
+            const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
+            const float rho = a.rho, r3 = a.r3;
+            float sr = fmaf(fmaf(fmaf(fmaf(q.R[5], rho, q.R[4]), rho, q.R[3]), rho, q.R[2]), rho, q.R[1]);
+            sr = fmaf(sr, rho, q.R[0]) * rho;
+            float si = fmaf(fmaf(fmaf(q.I[4], rho, q.I[3]), rho, q.I[2]), rho, q.I[1]);
+            si = fmaf(si, rho, q.I[0]) * r3;
+            S0h += Zr;
+            S0t = fmaf(Zr, sr, fmaf(-Zi, si, S0t));
+            Sih = fmaf(Zi, a.rh, Sih);
+            Sit = fmaf(fmaf(Zr, si, Zi * sr), a.rh, Sit);
+            float Ap = fmaf(fmaf(fmaf(fmaf(q.a[4], rho, q.a[3]), rho, q.a[2]), rho, q.a[1]), rho, q.a[0]);
+            Ap = fmaf(Ap, rho, -1.0f / 24.0f);
+            const float Bp = fmaf(fmaf(fmaf(q.b[3], rho, q.b[2]), rho, q.b[1]), rho, q.b[0]) * r3;
+            const float Cq = fmaf(fmaf(fmaf(q.c[3], rho, q.c[2]), rho, q.c[1]), rho, q.c[0]) * r3;
+            float Eq = fmaf(fmaf(fmaf(q.e[3], rho, q.e[2]), rho, q.e[1]), rho, q.e[0]);
+            Eq = fmaf(Eq, rho, 1.0f / 120.0f);
+            SA = fmaf(rho, fmaf(Zr, Ap, -Zi * Bp), SA);
+            SB = fmaf(r3, fmaf(Zr, Cq, -Zi * Eq), SB);
+        } else {
+            float cP, sP, cQ, sQ;
+            expm_turns_fast(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
+            expm_turns_fast(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
+            float scP, dscP, scQ, dscQ;
+            sincd32_inv(a.rh * q.hP0, a.rinv * rec.ihP, scP, dscP);
+            sincd32_inv(a.rh * q.hQ0, a.rinv * rec.ihQ, scQ, dscQ);
+            // X = E sinc(h), Y = i E sinc'(h); x = Re(conj r' X), y = Re(conj r' Y)
+            const float XPr = cP * scP, XPi = sP * scP, XQr = cQ * scQ, XQi = sQ * scQ;
+            xP = fmaf(rr, XPr, fmaf(ri, XPi, xP));
+            xQ = fmaf(rr, XQr, fmaf(ri, XQi, xQ));
+            yP = fmaf(dscP, fmaf(ri, cP, -rr * sP), yP);
+            yQ = fmaf(dscQ, fmaf(ri, cQ, -rr * sQ), yQ);
+            // Re(conj r' i (X_P - X_Q)) / r
+            G0 = fmaf(fmaf(ri, XPr - XQr, -rr * (XPi - XQi)), a.rinv, G0);
+        }
+    }
+}
+
 // A warp per (direction, triangle), its lanes on the radii: lane l takes radii
 // l, l + 32, ... of the direction, so the Taylor / largest-gap choice, which
 // moves with r, splits a warp at most once per record. Each lane combines its
@@ -807,57 +871,12 @@ __global__ void __launch_bounds__(ADJ_TPB) adjoint_kernel_radial(const TriRecF* 
                 const bool big = fabsf(q.dmh) * __int_as_float(s_rbits) >= 8192.0f;
                 float S0h = 0.0f, S0t = 0.0f, Sih = 0.0f, Sit = 0.0f, SA = 0.0f, SB = 0.0f;
                 float xP = 0.0f, yP = 0.0f, xQ = 0.0f, yQ = 0.0f, G0 = 0.0f;
-                for (int ir = lane; ir < n_rad; ir += 32) {
-                    const AdjRad a = rt[ir];
-                    const float4 w = sn[ir];
-                    const float rr = w.x, ri = w.y;
-                    const float P = a.rh * q.dmh;
-                    const float e = fmaf(a.rh, q.dmh, -P);
-                    float lo = fmaf(a.rh, q.dml, fmaf(a.rlo, q.dmh, e));
-                    float tau = (P - rintf(P)) - w.z;
-                    if (big) {
-                        const float tl2 = tau + lo;
-                        lo = two_sum_err(tau, lo, tl2);
-                        tau = tl2;
-                    }
-                    if (q.gmax0 < a.thr) {
-                        float c, s;
-                        expm_turns_fast(tl, tau, lo, c, s);
-                        const float Zr = fmaf(rr, c, ri * s), Zi = fmaf(rr, s, -ri * c);
-                        const float rho = a.rho, r3 = a.r3;
-                        float sr = fmaf(fmaf(fmaf(fmaf(q.R[5], rho, q.R[4]), rho, q.R[3]), rho, q.R[2]), rho, q.R[1]);
-                        sr = fmaf(sr, rho, q.R[0]) * rho;
-                        float si = fmaf(fmaf(fmaf(q.I[4], rho, q.I[3]), rho, q.I[2]), rho, q.I[1]);
-                        si = fmaf(si, rho, q.I[0]) * r3;
-                        S0h += Zr;
-                        S0t = fmaf(Zr, sr, fmaf(-Zi, si, S0t));
-                        Sih = fmaf(Zi, a.rh, Sih);
-                        Sit = fmaf(fmaf(Zr, si, Zi * sr), a.rh, Sit);
-                        float Ap = fmaf(fmaf(fmaf(fmaf(q.a[4], rho, q.a[3]), rho, q.a[2]), rho, q.a[1]), rho, q.a[0]);
-                        Ap = fmaf(Ap, rho, -1.0f / 24.0f);
-                        const float Bp = fmaf(fmaf(fmaf(q.b[3], rho, q.b[2]), rho, q.b[1]), rho, q.b[0]) * r3;
-                        const float Cq = fmaf(fmaf(fmaf(q.c[3], rho, q.c[2]), rho, q.c[1]), rho, q.c[0]) * r3;
-                        float Eq = fmaf(fmaf(fmaf(q.e[3], rho, q.e[2]), rho, q.e[1]), rho, q.e[0]);
-                        Eq = fmaf(Eq, rho, 1.0f / 120.0f);
-                        SA = fmaf(rho, fmaf(Zr, Ap, -Zi * Bp), SA);
-                        SB = fmaf(r3, fmaf(Zr, Cq, -Zi * Eq), SB);
-                    } else {
-                        float cP, sP, cQ, sQ;
-                        expm_turns_fast(tl, fmaf(a.rh, q.oPt, tau), lo, cP, sP);
-                        expm_turns_fast(tl, fmaf(a.rh, q.oQt, tau), lo, cQ, sQ);
-                        float scP, dscP, scQ, dscQ;
-                        sincd32_inv(a.rh * q.hP0, a.rinv * srec[j].ihP, scP, dscP);
-                        sincd32_inv(a.rh * q.hQ0, a.rinv * srec[j].ihQ, scQ, dscQ);
-                        // X = E sinc(h), Y = i E sinc'(h); x = Re(conj r' X), y = Re(conj r' Y)
-                        const float XPr = cP * scP, XPi = sP * scP, XQr = cQ * scQ, XQi = sQ * scQ;
-                        xP = fmaf(rr, XPr, fmaf(ri, XPi, xP));
-                        xQ = fmaf(rr, XQr, fmaf(ri, XQi, xQ));
-                        yP = fmaf(dscP, fmaf(ri, cP, -rr * sP), yP);
-                        yQ = fmaf(dscQ, fmaf(ri, cQ, -rr * sQ), yQ);
-                        // Re(conj r' i (X_P - X_Q)) / r
-                        G0 = fmaf(fmaf(ri, XPr - XQr, -rr * (XPi - XQi)), a.rinv, G0);
-                    }
-                }
+                if (big)
+                    adj_lane_radii<true>(rt, sn, srec[j], tl, lane, n_rad, S0h, S0t, Sih, Sit, SA, SB, xP, yP, xQ, yQ,
+                                         G0);
+                else
+                    adj_lane_radii<false>(rt, sn, srec[j], tl, lane, n_rad, S0h, S0t, Sih, Sit, SA, SB, xP, yP, xQ,
+                                          yQ, G0);
                 // this lane's share of sum_r rho_0, sum_r rho_i r, sum_r rho_1 r, sum_r rho_2 r
                 const float g1d = srec[j].d1, g2d = srec[j].d2;
                 const float ya = -(g1d + g2d) * (1.0f / 3.0f);
