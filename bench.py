@@ -76,13 +76,14 @@ def parse():
     p.add_argument("--serve-queries", type=int, default=2000)
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint batch and fitting measurement")
     p.add_argument("--no-paper", action="store_true", help="skip the paper's cube-rule refinement ladder")
-    p.add_argument("--case", choices=["adjoint-n16", "large-window", "large-dirs", "large"], default=None,
+    p.add_argument("--case", choices=["adjoint-n16", "large-window", "large-dirs", "large", "paper-n5"], default=None,
                    help="run one fixed case for a profiler and exit: adjoint-n16 = three mixed gradients of the "
                         "n=16 adjoint-configuration mesh (seed 0) on the 192x64x96 rule; large-window = two "
                         "mixed distances of the large query on radial shells 128-191 of its rule; large-dirs = "
                         "two mixed distances of the large mesh on every radial shell of the large rule with "
                         "1/16 of its directions (256 x 32 x 64 Hermitian: the same 256-radius blocks and row "
-                        "forms as the large launch); large = two mixed distances of the large query")
+                        "forms as the large launch); large = two mixed distances of the large query; paper-n5 "
+                        "= two mixed distances of T_5 on the paper's cube rule (xi_max = 5, M = 128, s = 10)")
     return p.parse_args()
 
 
@@ -634,6 +635,15 @@ def profile_case(name):
         out = torch.zeros(1, dtype=torch.float64, device="cuda")
         for _ in range(2):
             wd.wd_distance_dev(ctx.handle, rule, dv, dt, None, synth.LARGE_S, wd.WD_MIXED, out)
+        torch.cuda.synchronize()
+        print("D %.15e" % out.item())
+    elif name == "paper-n5":
+        rule = ctx.cube_rule(synth.PAPER_XI_MAX, synth.PAPER_M, True)
+        v, t = synth.icosphere_recursive(5)
+        dv, dt = torch.tensor(v, device="cuda"), torch.tensor(t, device="cuda", dtype=torch.int32)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            wd.wd_distance_dev(ctx.handle, rule, dv, dt, None, synth.PAPER_S, wd.WD_MIXED, out)
         torch.cuda.synchronize()
         print("D %.15e" % out.item())
     ctx.close()
