@@ -177,11 +177,12 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, floa
     ei = -s;
 }
 
-// expm_turns with a shorter residual: v = u + tlo stays in turns (one add),
-// and cos(2 pi v) - 1 and sin(2 pi v) are polynomials in v with the powers of
-// 2 pi folded into their coefficients, sin(2 pi v) as one float instead of a
-// float pair: one instruction fewer than the residual in radians.
-// The leading coefficients (2 pi)^2 / 2 and 2 pi are float pairs whose high
+// The residual part of the fast table exponential: table entry idx (of the
+// lane's replica) times exp(-2 pi i v), as (er, ei), for a residual v in turns,
+// |v| <= 1/256 + a few 2^-24. cos(2 pi v) - 1 and sin(2 pi v) are polynomials
+// in v with the powers of 2 pi folded into their coefficients, sin(2 pi v) as
+// one float instead of a float pair: one instruction fewer than a residual in
+// radians. The leading coefficients (2 pi)^2 / 2 and 2 pi are float pairs whose high
 // products enter each final FMA exactly. Rounded alone they would scale
 // every residual sine by 1 + 2.8e-8 and every cos - 1 by 1 - 2.9e-8; a kernel
 // whose residual v is not dithered (see node_dither_steps) sees those as a
@@ -191,8 +192,6 @@ __device__ __forceinline__ void expm_turns(const TabEntry* __restrict__ tl, floa
 // |v| <= 1/256 + |tlo|: the rounding of v is below 2.5e-10 turns, that of
 // sin(2 pi v) below 1.5e-9, and the dropped v^5 (sine) and v^6 (cosine)
 // terms below 7.5e-11, all far below the 6e-8 rounding of the result.
-// The residual part of expm_turns_fast: table entry idx (of the lane's
-// replica) times exp(-2 pi i v), |v| <= 1/256 + a few 2^-24, as (er, ei).
 __device__ __forceinline__ void expm_residual(const TabEntry* __restrict__ tl, int idx, float v, float& er,
                                               float& ei)
 {
@@ -228,6 +227,7 @@ __device__ __forceinline__ void expm_residual_wide(const TabEntry* __restrict__ 
     ei = -s;
 }
 
+// expm_turns with the residual u + tlo in turns (expm_residual)
 __device__ __forceinline__ void expm_turns_fast(const TabEntry* __restrict__ tl, float tau, float tlo, float& er,
                                                 float& ei, float magic = kMagic)
 {
@@ -273,9 +273,6 @@ __device__ __forceinline__ void unshift_add(const TabEntry* __restrict__ tab, in
     ai += sr * sn + si * c;
 }
 
-// Kahan-compensated float32 accumulation: the per-tile sum of nearly equal
-// terms at low frequency would otherwise round the same way at neighbouring
-// nodes, a coherent error that the mesh-minus-sphere difference magnifies.
 // rounding error of s = fl(a + b): a + b = s + err exactly (Knuth's two-sum)
 __device__ __forceinline__ float two_sum_err(float a, float b, float s)
 {
@@ -283,6 +280,9 @@ __device__ __forceinline__ float two_sum_err(float a, float b, float s)
     return (a - (s - bb)) + (b - bb);
 }
 
+// Kahan-compensated float32 accumulation: the per-tile sum of nearly equal
+// terms at low frequency would otherwise round the same way at neighbouring
+// nodes, a coherent error that the mesh-minus-sphere difference magnifies.
 struct Kahan {
     float s = 0.0f, c = 0.0f;
     __device__ __forceinline__ void add(float x)
