@@ -1537,8 +1537,9 @@ __device__ __forceinline__ void radial_sum(RadRec* tile, const TabEntry* __restr
             const int n8 = cnt8 - seg < 64 ? cnt8 - seg : 64;
             const int k = (h.dl * S::TILE + seg) >> 5;  // the segment's two 32-record maxima
             const float gap = __uint_as_float(max(s_gmax[k], s_gmax[k + 1])) * rmax;  // bounds every lane's gaps
-            // the table exponential takes the unreduced phase while |128 P|
-            // stays well inside the magic constant's 2^22 integer range
+            // radial_expm takes the unreduced phase P while |P| < 2^13 turns,
+            // well inside the [-2^15, 2^15) where adding kMagicTurns keeps the
+            // sum on the grid of table steps
             if (__uint_as_float(max(s_pmax[k], s_pmax[k + 1])) * rmax >= 8192.0f)
                 radial_row<3>(tl, rec + seg, n8, h, kr, ki);
             else if (gap < kDeltaShort32)
