@@ -208,8 +208,9 @@ __device__ __forceinline__ void expm_residual(const TabEntry* __restrict__ tl, i
 }
 
 // expm_residual for |v| <= 1/128 + a few 2^-24 (two table steps): the sine to
-// v^5 and the cosine to v^6 (the first dropped terms below 1.5e-13), for a
-// kernel whose residual is the sum of two table-step residuals.
+// v^5 and the cosine to v^6 (the first dropped terms below 1.5e-13; the float
+// cubic coefficient adds up to 6e-13), for a kernel whose residual is the sum
+// of two table-step residuals.
 __device__ __forceinline__ void expm_residual_wide(const TabEntry* __restrict__ tl, int idx, float v, float& er,
                                                    float& ei)
 {
