@@ -72,3 +72,31 @@ def test_the_range_limit_is_real():
     mt = MAGIC_TURNS
     m = round_f32(Fraction(40000) + Fraction(1, 300) + mt)
     assert m >= 2 ** 17 and (m * 128).denominator == 1 and int(m * 128) % 2 == 0  # grid 2^-6: steps lost
+
+
+def test_lattice_lookup_steps_are_exact():
+    """The lattice kernel's variant: the record holds its phase at i = 0, t0h
+    (reduced mod 1, a float), as S0 table steps inside mt0 = 1.5 * 2^16 +
+    S0/128 plus t0r = t0h - S0/128; the pair's phase i rh + t0h is then table
+    entry K + S0 (the low bits of fl(i rh + mt0)) plus the residual
+    fl(i rh - K/128) + t0r, at most two table steps."""
+    rng = np.random.default_rng(5)
+    for _ in range(2000):
+        t0h = f32(rng.uniform(-0.5, 0.5))
+        rh = f32(rng.uniform(-1.0, 1.0))
+        i = int(rng.integers(-64, 65))
+        S0 = round(t0h * 128)  # rintf (ties to even) of an exact product
+        mt0 = MAGIC_TURNS + Fraction(S0, 128)
+        assert round_f32(mt0) == mt0
+        t0r = round_f32(t0h - Fraction(S0, 128))
+        assert t0r == t0h - Fraction(S0, 128) and abs(t0r) <= Fraction(1, 256)  # exact
+        P = i * rh  # exact inside the FMA
+        m = round_f32(P + mt0)
+        idx = int(m * 128) % 128
+        nk = mt0 - m
+        assert round_f32(nk) == nk and (nk * 128).denominator == 1
+        u = round_f32(P + nk)
+        v = round_f32(u + t0r)
+        assert abs(v) <= Fraction(1, 128) + Fraction(1, 2 ** 30)
+        phase = (Fraction(idx, 128) + v) % 1
+        assert abs((phase - (P + t0h) % 1 + Fraction(1, 2)) % 1 - Fraction(1, 2)) <= Fraction(1, 2 ** 31)
